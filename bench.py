@@ -1,0 +1,388 @@
+"""Benchmark: Gcell-updates/s of the two-fluid Yee step on the CPW resonator
+(512 x 256 x 128 cells, CPML 12, London + Ohmic films, soft source, two
+64-frequency probe DFTs), plus the HBM roofline fraction of the dominant
+kernel, an end-to-end number through the C ABI with host buffers, and the
+FP64 CPU oracle on the same workload as the baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as N independent replicas (one resonator variant
+per rank, no collective on the data path); `value` is the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s & HBM roofline fraction; batched and adjoint vs plain step"
+UNIT = "Gcell-updates/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+# ------------------------------------------------------------------ ranks
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_seed(rank: int) -> int:
+    """Replica r draws its own sigma map (a different resonator variant)."""
+    from paper_2305_13419_gb300 import workloads as W
+    return W.BASE_SEED + 2 + 1000 * rank
+
+
+def aggregate(cells_per_rank, steps, max_ms, world):
+    """Whole-job throughput: all ranks' cell-updates over the slowest rank's time."""
+    return cells_per_rank * steps * world / (max_ms * 1e-3) / 1e9
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline
+def algorithmic_bytes(w, N):
+    """Algorithmic HBM bytes per launch of the two step kernels (each array
+    element read or written once, FP32): update_B reads E and reads + writes
+    B (36 B/point) and reads + writes psi_B on CPML slab points (8 B each);
+    update_E reads B, reads + writes E, reads eps, sigma, kappa maps
+    (48 B/point), reads + writes Js on superconducting edges (8 B each) and
+    psi_E on slab points (8 B each)."""
+    pts = int(N[0]) * int(N[1]) * int(N[2])
+    psi = 0
+    for a in range(3):
+        if w.bc[a] != "cpml":
+            continue
+        L = w.cpml[a].ncells
+        other = pts // N[a]
+        psi += 2 * (2 * L) * other          # two psi arrays per slab axis, 2L planes
+    sc = w.lambda_L > 0
+    sc_edges = 0
+    for c in range(3):                     # E_c edge is SC if any of its 4 cells is
+        ax = [2 - b for b in range(3) if b != c]   # numpy axes of the two transverse directions
+        m = sc.copy()
+        for a in ax:
+            m = m | np.roll(m, 1, axis=a)
+        sc_edges += int(m.sum())
+    b_bytes = 36 * pts + 8 * psi
+    e_bytes = 48 * pts + 8 * psi + 8 * sc_edges
+    return {"update_B": b_bytes, "update_E": e_bytes, "points": pts, "sc_edges": sc_edges, "psi_points": psi}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2305_13419_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except ValueError:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch_fullsize")
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return float(json.load(open(p))["hbm_gbs"]), "measured"
+        except (ValueError, KeyError):
+            pass
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU baseline
+def cpu_baseline(w, budget_s=10.0):
+    """The FP64 oracle as it stands, on this host's cores, stepping the same
+    workload from rest until `budget_s` of stepping has elapsed."""
+    from oracle import stepper
+    threads = stepper.set_threads(os.cpu_count() or 1)
+    g = stepper.Grid.from_workload(w)
+    g.step(1)                       # first step outside the clock (psi init, page faults)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        g.step(1)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s and n >= 2:
+            break
+    el = time.perf_counter() - t0
+    return {"value": w.ncells * n / el / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{w.name}: {n} FP64 oracle steps after one untimed step ({el:.1f} s)"}
+
+
+def reference_sample_workload():
+    """Bounded sample of the CPW workload for the oracle arm: a 128 x 128 x 64
+    cell block cut from it around the in-port / resonator gap at the film
+    plane, closed with PEC walls."""
+    from paper_2305_13419_gb300 import workloads as W
+    w = W.cpw()
+    sl = (slice(0, 64), slice(64, 192), slice(48, 176))
+    return W.Workload(name="cpw-512x256x128[48:176,64:192,0:64]", n=(128, 128, 64), d=w.d, theta=w.theta,
+                      bc=("pec", "pec", "pec"), eps_r=np.ascontiguousarray(w.eps_r[sl]),
+                      mu_r=np.ascontiguousarray(w.mu_r[sl]), lambda_L=np.ascontiguousarray(w.lambda_L[sl]),
+                      sigma=np.ascontiguousarray(w.sigma[sl]), courant=w.courant)
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    from oracle import stepper
+    w = reference_sample_workload()
+    threads = stepper.set_threads(os.cpu_count() or 1)
+    g = stepper.Grid.from_workload(w)
+    g.step(args.warmup)
+    t0 = time.perf_counter()
+    g.step(args.steps)
+    el = time.perf_counter() - t0
+    v = w.ncells * args.steps / el / 1e9
+    sample = f"{w.name}: {args.steps} FP64 oracle steps on a 1/16 block of the workload"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_block(state_bytes=None):
+    c = {"workload": "cpw-512x256x128: CPW resonator, CPML 12, lambda_L = 3 cells, sigma_n ~ U[0,1e6] S/m, "
+                     "theta = 1, Courant 0.95, +/- Gaussian-sine port source, 2 probes x 64-frequency DFT",
+         "cells": 512 * 256 * 128, "parallelism": "replicas (independent resonator per GPU)"}
+    if state_bytes:
+        c["l2"] = f"inputs larger than L2: {state_bytes / 2**20:.0f} MiB of fields and maps per step > 129 MiB"
+    return c
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2305_13419_gb300 import twofluid as tf
+    from paper_2305_13419_gb300 import workloads as W
+
+    dist = init_dist(ws, "nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.cpw(seed=replica_seed(rank))
+    g = tf.Grid.from_workload(w)
+    N = g.N
+    ab = algorithmic_bytes(w, N)
+    state_bytes = (9 + 3) * 4 * ab["points"]
+
+    # device-timed throughput: inputs resident in HBM, K steps between barriers
+    g.step(args.warmup)
+    g.sync()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(g.stream)
+        g.step(args.steps)
+        stop.record(g.stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms = start.elapsed_time(stop)
+    g.sync()
+    ms_max = max_over_ranks(dist, ms, dev)
+    value = aggregate(w.ncells, args.steps, ms_max, ws)
+
+    # per-kernel durations over the same number of steps (events around each launch)
+    kt = g.step_timed(args.steps)
+    g.sync()
+    dom = max(("update_B", "update_E"), key=lambda k: kt[k][0])
+    peak, peak_kind = hbm_peak()
+    achieved = ab[dom] / (kt[dom][0] * 1e-3) / 1e9
+    traffic = ncu_traffic("k_" + dom)
+    roof = {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": ab[dom],
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+            "kernel_ms": {k: v[0] for k, v in kt.items()}}
+    launches_per_step = sum(1 for k in kt)  # probe, B, E (+ Mur)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, w, dev)
+
+    base = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(w, budget_s=args.cpu_budget)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_block(state_bytes), "roofline": roof, "cpu_baseline": base, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, w, dev):
+    """Same metric through the public API from host memory: the timed region
+    uploads the material maps from pinned host buffers, runs the K steps and
+    reads back both probe DFTs and the integer-level Ex field into pinned
+    host memory."""
+    import torch
+    from paper_2305_13419_gb300 import twofluid as tf
+    g = tf.Grid(w.n, w.d, w.theta, w.bc, w.cpml, courant=w.courant, device=dev)
+    cs = (w.n[2], w.n[1], w.n[0])
+    maps = []
+    for a in (w.eps_r, w.mu_r, w.lambda_L, w.sigma):
+        t = torch.empty(cs, dtype=torch.float32, pin_memory=True)
+        t.numpy()[...] = a
+        maps.append(t)
+    out = torch.empty(g.shape, dtype=torch.float32, pin_memory=True)
+    for s in w.sources:
+        g.add_source(s.comp, s.lo, s.hi, s.amp, s.kind, s.f, s.t0, s.tw)
+    for p in w.probes:
+        g.add_probe(p.comp, p.p, p.freqs, p.n0)
+    import ctypes as C
+    L = tf.load()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc = L.tf_set_materials(g.h, *[int(m.data_ptr()) for m in maps], 0)
+    assert rc == 0, rc
+    g.step(args.steps)
+    spectra = [g.probe_dft(p) for p in range(len(w.probes))]
+    rc = L.tf_read_field(g.h, 0, int(out.data_ptr()), 0)
+    assert rc == 0, rc
+    g.sync()
+    el = time.perf_counter() - t0
+    h2d = 4 * 4 * w.ncells
+    d2h = 16 * sum(s.size for s in spectra) + 4 * int(np.prod(g.shape))
+    g.close()
+    return {"value": w.ncells * args.steps / el / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    args = ap.parse_args(argv)
+    ws, rank, local = dist_env()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,200 @@
+/*
+ * twofluid.h -- C ABI of the GB300 two-fluid (Maxwell + London + Ohmic)
+ * Yee FDTD library, after arXiv 2305.13419.
+ *
+ * Model (Sec. 2, Eqs. Ampere, Faraday, London1a):
+ *     curl H = sigma_n E + Js + eps dE/dt,   curl E = -dB/dt,
+ *     dJs/dt = E / (lambda_L^2 mu),           B = mu H.
+ * Discretisation (Sec. 3, Algorithm 1): Yee grid, E on edges at integer time
+ * levels, B on faces and Js on E edges at half levels; the Ohmic current is
+ * taken with the theta scheme of Alg. 1 step 3.  The library advances the
+ * algebraically identical fused leapfrog (Alg. 1 steps 5+1 and 4+2 merged),
+ * so one tf_step() call of N steps moves (E^n, B^{n-1/2}, Js^{n-1/2}) to
+ * (E^{n+N}, B^{n+N-1/2}, Js^{n+N-1/2}); field reads return integer levels.
+ *
+ * Grid and storage convention (shared by every call that takes a field):
+ *   - nx, ny, nz cells of size dx, dy, dz.  An axis has N = n points when it
+ *     is periodic and N = n + 1 points (both walls) otherwise.
+ *   - field arrays are dense float32 [Nz][Ny][Nx] (x fastest).  Point (i,j,k)
+ *     holds Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2) Bx(i,j+1/2,k+1/2)
+ *     By(i+1/2,j,k+1/2) Bz(i+1/2,j+1/2,k) and Js on the E positions.  Values
+ *     that fall outside the domain, tangential E on PEC/CPML walls and normal
+ *     B on walls are held at zero; Js is held at zero on edges whose material
+ *     is not superconducting.
+ *   - material maps are dense float32 [nz][ny][nx] over cells.
+ *   - units are SI (V/m, T, A/m^2, S/m, m, s).
+ *
+ * Errors: every call returns a tf_status; nothing is reported any other way.
+ * Arguments are validated before any GPU work is enqueued.  Device faults and
+ * the non-finite watchdog are latched and surface at tf_sync().
+ *
+ * Ownership: the caller owns the device workspace (tf_workspace_size bytes)
+ * and every host or device buffer passed in; the library copies what it
+ * keeps and never allocates device memory.  A handle is not thread-safe; all
+ * GPU work of a handle is enqueued on the stream given in its descriptor.
+ */
+#ifndef TWOFLUID_H
+#define TWOFLUID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TF_MAX_PROBES 16
+#define TF_MAX_FREQS 64
+#define TF_MAX_SOURCES 16
+
+typedef struct tf_ctx* tf_handle;
+
+typedef enum {
+    TF_OK = 0,
+    TF_EINVAL = 1,      /* bad argument (null pointer, out of range, bad descriptor) */
+    TF_ENOMEM = 2,      /* workspace smaller than tf_workspace_size() */
+    TF_ECUDA = 3,       /* a CUDA runtime call failed (launch, copy, device fault) */
+    TF_EUNSTABLE = 4,   /* time step violates the stability bound of the scheme */
+    TF_ESTATE = 5,      /* call not allowed in the handle's current state */
+    TF_ETIMEOUT = 6,    /* a bounded device wait gave up */
+    TF_ENONFINITE = 7,  /* the watchdog saw a non-finite E value */
+    TF_ENOTSUP = 8      /* valid request this build does not support */
+} tf_status;
+
+/* boundary kinds (Sec. 3: periodic, PEC and PML; Mur offered for quasi-1-D runs) */
+enum { TF_BC_PERIODIC = 0, TF_BC_PEC = 1, TF_BC_MUR = 2, TF_BC_CPML = 3 };
+/* soft-source waveforms s(t) (Secs. 4.1, 4.2, 5):
+ *   GAUSS     exp(-(t-t0)^2 / (2 tw^2))
+ *   SIN       sin(2 pi f t)
+ *   GAUSS_SIN exp(-(t-t0)^2 / (2 tw^2)) sin(2 pi f t)                 */
+enum { TF_SRC_GAUSS = 0, TF_SRC_SIN = 1, TF_SRC_GAUSS_SIN = 2 };
+enum { TF_EX = 0, TF_EY, TF_EZ, TF_BX, TF_BY, TF_BZ, TF_JSX, TF_JSY, TF_JSZ };
+/* edge material rule (Sec. 3: edges on an SC interface are superconducting) */
+enum { TF_EDGE_CONDUCTOR_MEAN = 0, TF_EDGE_PLAIN_MEAN = 1 };
+
+/* One axis' boundary, applied to both of its faces.
+ *   TF_BC_CPML: Roden-Gedney convolutional PML, kappa = 1, backed by PEC;
+ *     over `cpml_cells` cells the conductivity grows as
+ *     sigma_max rho^order and the frequency shift falls as alpha_max (1-rho),
+ *     rho = depth into the layer / cpml_cells.  2 cpml_cells <= n.
+ *   TF_BC_MUR: first-order Mur, z axis only.                              */
+typedef struct {
+    int kind;
+    int cpml_cells;
+    double cpml_order;
+    double cpml_sigma_max;   /* S/m */
+    double cpml_alpha_max;   /* S/m */
+} tf_bc;
+
+typedef struct {
+    int nx, ny, nz;          /* cells, each >= 1 */
+    double dx, dy, dz;       /* m, > 0 */
+    double dt;               /* s; if <= 0, dt = courant / (c sqrt(1/dx^2+1/dy^2+1/dz^2)) */
+    double courant;          /* used only when dt <= 0; the paper's convention (Secs. 4-5) */
+    double theta;            /* Ohmic time weighting of Alg. 1 step 3, in [0.5, 1] */
+    tf_bc bc[3];             /* x, y, z */
+    int edge_rule;           /* TF_EDGE_* */
+    int max_probes;          /* 0 .. TF_MAX_PROBES */
+    int64_t series_capacity; /* time levels each probe may record (0 = none) */
+    void* stream;            /* cudaStream_t for all GPU work of the handle (NULL = default) */
+} tf_grid_desc;
+
+/* Bytes of device workspace a grid with this descriptor needs; 0 if the
+ * descriptor is invalid.  Host-only, no GPU call. */
+size_t tf_workspace_size(const tf_grid_desc* desc);
+
+/* Create a grid in the caller's device workspace (>= tf_workspace_size bytes,
+ * 256-byte aligned).  Fields start at zero, materials at vacuum
+ * (eps_r = mu_r = 1, lambda_L = 0, sigma = 0).  *out receives the handle.
+ * TF_EINVAL bad descriptor, TF_ENOMEM workspace too small, TF_ENOTSUP Mur on x/y,
+ * TF_ECUDA failed clears. */
+tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes, tf_handle* out);
+
+/* Release the host side of the handle (the workspace stays the caller's). */
+tf_status tf_destroy(tf_handle h);
+
+/* Storage points per axis (N = n, or n + 1 on a non-periodic axis). */
+tf_status tf_storage_dims(tf_handle h, int dims[3]);
+
+/* Current integer level n and time n * dt; dt of the grid. */
+tf_status tf_get_time(tf_handle h, int64_t* n, double* t);
+tf_status tf_get_dt(tf_handle h, double* dt);
+
+/* Per-cell material maps (Sec. 2: eps = eps0 eps_r, mu = mu0 mu_r, lambda_L
+ * London depth, sigma normal-fluid conductivity; Sec. 3: 1/lambda -> 0 off
+ * the superconductor, so lambda_L = 0 marks a non-superconducting cell).
+ * Dense [nz][ny][nx] float32, host (on_device = 0) or device pointers; NULL
+ * keeps the vacuum default for that map.  Copied; the caller keeps ownership.
+ * Edge values: eps is the mean over the four cells sharing an edge; sigma and
+ * kappa = 1/(lambda^2 mu) follow edge_rule; a face takes the mean mu of its two
+ * cells.  Only before the first tf_step().  Checks eps_r, mu_r > 0,
+ * sigma >= 0, lambda_L >= 0 (TF_EINVAL) and the stability bound
+ * C^2 max 1/(eps_r mu_r) + max (c dt / (2 lambda_L))^2 / (eps_r mu_r) <= 1 (TF_EUNSTABLE).
+ * Synchronises the handle's stream. */
+tf_status tf_set_materials(tf_handle h, const float* eps_r, const float* mu_r,
+                           const float* lambda_L, const float* sigma, int on_device);
+
+/* Initial value (level 0) of one component, SI, dense [Nz][Ny][Nx] float32,
+ * host or device.  Only before the first tf_step() (TF_ESTATE otherwise).
+ * Points the convention holds at zero are zeroed. */
+tf_status tf_set_field(tf_handle h, int comp, const float* src, int on_device);
+
+/* Soft source (Secs. 4.2, 5): after each E update, E_comp += amp * s(t^{n+1})
+ * on every advanced E_comp point of the storage box [lo, hi).  comp in
+ * TF_EX..TF_EZ; up to TF_MAX_SOURCES; *id (may be NULL) receives its index. */
+tf_status tf_add_source(tf_handle h, int comp, const int lo[3], const int hi[3], double amp,
+                        int kind, double f, double t0, double tw, int* id);
+
+/* Point probe with a running FP64 DFT (Sec. 4.2 Fourier-transforms probe
+ * signals, Sec. 5 extracts Q from them): at the start of every step n the
+ * library samples s^n = E_comp(p) and, for n >= n0, adds
+ * s^n exp(-i 2 pi frac(f_k dt n)) dt to X_k, k < nfreq <= TF_MAX_FREQS.
+ * With series_capacity > 0 it also records s^n for n < series_capacity.
+ * Up to max_probes; *id (may be NULL) receives its index. */
+tf_status tf_add_probe(tf_handle h, int comp, const int p[3], const double* freqs, int nfreq,
+                       int64_t n0, int* id);
+
+/* Advance nsteps >= 0 steps of Algorithm 1 (fused form) on the stream:
+ * probe sample, B update with CPML memory, Js update, theta-scheme E update
+ * with sources, Mur walls.  Asynchronous; errors of the launches are
+ * returned, device-side errors latch for tf_sync(). */
+tf_status tf_step(tf_handle h, int64_t nsteps);
+
+/* tf_step with per-kernel timing (the library's profiling hook): advances
+ * nsteps exactly like tf_step and records a CUDA event pair on the handle's
+ * stream around every kernel it launches.  On return (the stream is
+ * synchronised) kernel_ms[k] is the mean duration in ms of one launch of
+ * kernel kind k and launches[k] the number of launches, for k = 0 probe DFT,
+ * 1 B update, 2 E update, 3 Mur walls (arrays of nkinds <= 4 entries). */
+tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds);
+
+/* Wait for the stream and return the latched device status
+ * (TF_ENONFINITE if the watchdog saw a non-finite E). */
+tf_status tf_sync(tf_handle h);
+
+/* Copy probe id's DFT accumulators (FP64, nfreq values each) to host arrays. */
+tf_status tf_read_probe_dft(tf_handle h, int id, double* re, double* im);
+
+/* Copy the first n recorded samples (n <= min(level, series_capacity)). */
+tf_status tf_read_probe_series(tf_handle h, int id, double* out, int64_t n);
+
+/* Integer-level value of one component at the current level (Alg. 1 steps
+ * 4-5 applied to the half-level state: B^n = B^{n-1/2} - dt/2 curl E^n,
+ * Js^n = Js^{n-1/2} + dt/2 E^n/(lambda^2 mu)), SI, dense [Nz][Ny][Nx]
+ * float32 into a host or device buffer.  Synchronises the stream. */
+tf_status tf_read_field(tf_handle h, int comp, float* dst, int on_device);
+
+/* Q-factor of one damped mode from probe id's DFT (Sec. 5 reports Q and the
+ * resonance from the ring-down): fits X_k = dt sum_{n0<=n<N} (a z^n + c.c.)
+ * w_k^n, z = exp((-alpha + i omega0) dt), in FP64 on the GPU.  f_guess and
+ * q_guess start the search (f_guess <= 0: the strongest bin).  Outputs
+ * f0 (Hz), alpha (1/s) and Q = omega0 / (2 alpha); any output may be NULL. */
+tf_status tf_fit_q(tf_handle h, int id, double f_guess, double q_guess, double* f0,
+                   double* alpha, double* q);
+
+const char* tf_strerror(tf_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

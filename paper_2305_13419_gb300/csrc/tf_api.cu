@@ -1,0 +1,552 @@
+// tf_api.cu -- the C ABI of include/twofluid.h: descriptor validation,
+// workspace carving, coefficient set-up and the per-step launch sequence.
+// All GPU work runs in the kernels of tf_kernels.cu / tf_fit.cu.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "tf_internal.cuh"
+
+using namespace tf;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct Layout {
+    int N[3], pitch;
+    long long total;        // floats per field array (padded)
+    long long ncell, ndense;
+    int ncpml_pairs;        // (component, axis) pairs carrying psi
+    size_t off_fields, off_maps, off_psi, off_prof, off_mur, off_probe, off_series, off_scratch,
+        off_misc, bytes;
+    long long scratch_floats;
+};
+
+double dt_of(const tf_grid_desc* d) {
+    if (d->dt > 0) return d->dt;
+    return d->courant / (kC0 * sqrt(1.0 / (d->dx * d->dx) + 1.0 / (d->dy * d->dy) + 1.0 / (d->dz * d->dz)));
+}
+
+tf_status validate(const tf_grid_desc* d) {
+    if (!d) return TF_EINVAL;
+    const int n[3] = {d->nx, d->ny, d->nz};
+    const double h[3] = {d->dx, d->dy, d->dz};
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 1 || !(h[a] > 0) || !isfinite(h[a])) return TF_EINVAL;
+        const tf_bc& b = d->bc[a];
+        if (b.kind < TF_BC_PERIODIC || b.kind > TF_BC_CPML) return TF_EINVAL;
+        if (b.kind == TF_BC_MUR && a != 2) return TF_ENOTSUP;
+        if (b.kind == TF_BC_MUR && n[a] < 2) return TF_EINVAL;
+        if (b.kind == TF_BC_CPML) {
+            if (b.cpml_cells < 1 || 2 * b.cpml_cells > n[a]) return TF_EINVAL;
+            if (!(b.cpml_order >= 0) || !(b.cpml_sigma_max >= 0) || !(b.cpml_alpha_max >= 0)) return TF_EINVAL;
+        }
+    }
+    if (!(d->dt > 0) && !(d->courant > 0)) return TF_EINVAL;
+    if (!(d->theta >= 0.5 && d->theta <= 1.0)) return TF_EINVAL;
+    if (d->edge_rule != TF_EDGE_CONDUCTOR_MEAN && d->edge_rule != TF_EDGE_PLAIN_MEAN) return TF_EINVAL;
+    if (d->max_probes < 0 || d->max_probes > TF_MAX_PROBES || d->series_capacity < 0) return TF_EINVAL;
+    const long long pts = (long long)(n[0] + 1) * (n[1] + 1) * (n[2] + 1);
+    if (pts > (1LL << 40)) return TF_EINVAL;
+    return TF_OK;
+}
+
+Layout layout_of(const tf_grid_desc* d) {
+    Layout L{};
+    const int n[3] = {d->nx, d->ny, d->nz};
+    for (int a = 0; a < 3; ++a) L.N[a] = n[a] + (d->bc[a].kind == TF_BC_PERIODIC ? 0 : 1);
+    L.pitch = (L.N[0] + 31) / 32 * 32;
+    L.total = (long long)L.pitch * L.N[1] * L.N[2];
+    L.ncell = (long long)n[0] * n[1] * n[2];
+    L.ndense = (long long)L.N[0] * L.N[1] * L.N[2];
+    L.ncpml_pairs = 0;
+    for (int a = 0; a < 3; ++a)
+        if (d->bc[a].kind == TF_BC_CPML) L.ncpml_pairs += 2;
+    const size_t fbytes = align_up(sizeof(float) * (size_t)L.total);
+    size_t o = 0;
+    L.off_fields = o; o += 9 * fbytes;
+    L.off_maps = o;   o += 4 * fbytes;
+    L.off_psi = o;    o += 2 * (size_t)L.ncpml_pairs * fbytes;
+    L.off_prof = o;
+    for (int a = 0; a < 3; ++a) o += 4 * align_up(sizeof(float) * (size_t)L.N[a]);
+    L.off_mur = o;    o += (d->bc[2].kind == TF_BC_MUR) ? 4 * align_up(sizeof(float) * (size_t)L.pitch * L.N[1]) : 0;
+    L.off_probe = o;  o += 3 * align_up(sizeof(double) * TF_MAX_PROBES * TF_MAX_FREQS);
+    L.off_series = o; o += align_up(sizeof(double) * (size_t)d->max_probes * (size_t)d->series_capacity);
+    L.scratch_floats = 4 * L.ncell > L.ndense ? 4 * L.ncell : L.ndense;
+    L.off_scratch = o; o += align_up(sizeof(float) * (size_t)L.scratch_floats);
+    L.off_misc = o;   o += kAlign;
+    L.bytes = o;
+    return L;
+}
+
+struct SrcHost {
+    int comp, lo[3], hi[3], kind;
+    double amp, f, t0, tw;
+};
+
+double waveform(const SrcHost& s, double t) {
+    const double env = exp(-(t - s.t0) * (t - s.t0) / (2.0 * s.tw * s.tw));
+    const double two_pi = 6.283185307179586476925286766559;
+    switch (s.kind) {
+        case TF_SRC_GAUSS: return env;
+        case TF_SRC_SIN: return sin(two_pi * s.f * t);
+        default: return env * sin(two_pi * s.f * t);
+    }
+}
+
+}  // namespace
+
+struct tf_ctx {
+    tf_grid_desc desc;
+    Layout L;
+    Params P;
+    Probes R;
+    cudaStream_t stream;
+    double dt;
+    long long level;
+    int primed;
+    char* ws;
+    float* scratch;
+    unsigned* status;
+    unsigned* mm;      // 4 words: max 1/(eps mu), max kt/(4 eps), non-uniform mu, spare
+    double* fit_out;   // 4 doubles
+    int nsrc;
+    SrcHost src[TF_MAX_SOURCES];
+    double freqs[TF_MAX_PROBES][TF_MAX_FREQS];
+};
+
+#define TF_CUDA(x)                                  \
+    do {                                            \
+        if ((x) != cudaSuccess) return TF_ECUDA;    \
+    } while (0)
+
+extern "C" {
+
+const char* tf_strerror(tf_status s) {
+    switch (s) {
+        case TF_OK: return "ok";
+        case TF_EINVAL: return "invalid argument";
+        case TF_ENOMEM: return "workspace too small";
+        case TF_ECUDA: return "CUDA error";
+        case TF_EUNSTABLE: return "time step violates the stability bound";
+        case TF_ESTATE: return "call not allowed in this state";
+        case TF_ETIMEOUT: return "device wait timed out";
+        case TF_ENONFINITE: return "non-finite field value";
+        case TF_ENOTSUP: return "not supported";
+    }
+    return "unknown status";
+}
+
+size_t tf_workspace_size(const tf_grid_desc* desc) {
+    if (validate(desc) != TF_OK) return 0;
+    return layout_of(desc).bytes;
+}
+
+static void cpml_profile(const tf_grid_desc* d, int a, double dt, double x, double r, float* b, float* c) {
+    const int n[3] = {d->nx, d->ny, d->nz};
+    const tf_bc& bc = d->bc[a];
+    const double L = bc.cpml_cells;
+    double rho = 0.0;
+    if (x < L) rho = (L - x) / L;
+    else if (x > n[a] - L) rho = (x - (n[a] - L)) / L;
+    if (rho <= 0.0) { *b = 0.f; *c = 0.f; return; }
+    const double s = bc.cpml_sigma_max * pow(rho, bc.cpml_order);
+    const double al = bc.cpml_alpha_max * (1.0 - rho);
+    const double bb = exp(-(s + al) * dt / kEps0);
+    const double cc = (s + al > 0.0) ? s * (bb - 1.0) / (s + al) : 0.0;
+    *b = (float)bb;
+    *c = (float)(cc * r);   // folded with r_a = c0 dt / d_a (scaled units)
+}
+
+tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes, tf_handle* out) {
+    if (!out || !dev_workspace) return TF_EINVAL;
+    *out = nullptr;
+    tf_status v = validate(desc);
+    if (v != TF_OK) return v;
+    if (((uintptr_t)dev_workspace) % kAlign) return TF_EINVAL;
+    const Layout L = layout_of(desc);
+    if (bytes < L.bytes) return TF_ENOMEM;
+    const double dt = dt_of(desc);
+    const double cour = kC0 * dt * sqrt(1.0 / (desc->dx * desc->dx) + 1.0 / (desc->dy * desc->dy) +
+                                        1.0 / (desc->dz * desc->dz));
+    if (!(cour <= 1.0)) return TF_EUNSTABLE;
+
+    tf_ctx* h = new (std::nothrow) tf_ctx();
+    if (!h) return TF_ENOMEM;
+    h->desc = *desc;
+    h->L = L;
+    h->dt = dt;
+    h->stream = (cudaStream_t)desc->stream;
+    h->ws = (char*)dev_workspace;
+    Params& P = h->P;
+    const int n[3] = {desc->nx, desc->ny, desc->nz};
+    const double dd[3] = {desc->dx, desc->dy, desc->dz};
+    for (int a = 0; a < 3; ++a) {
+        P.N[a] = L.N[a];
+        P.n[a] = n[a];
+        P.bc[a] = desc->bc[a].kind;
+        P.per[a] = desc->bc[a].kind == TF_BC_PERIODIC;
+        P.L[a] = desc->bc[a].kind == TF_BC_CPML ? desc->bc[a].cpml_cells : 0;
+        P.r[a] = (float)(kC0 * dt / dd[a]);
+    }
+    P.pitch = L.pitch;
+    P.plane = (long long)L.pitch * L.N[1];
+    P.theta = (float)desc->theta;
+    P.edge_rule = desc->edge_rule;
+    P.uniform_mu = 1;
+    P.mur_M = (float)((kC0 * dt - desc->dz) / (kC0 * dt + desc->dz));
+    const size_t fbytes = align_up(sizeof(float) * (size_t)L.total);
+    char* base = h->ws;
+    for (int c = 0; c < 3; ++c) {
+        P.E[c] = (float*)(base + L.off_fields + (0 + c) * fbytes);
+        P.B[c] = (float*)(base + L.off_fields + (3 + c) * fbytes);
+        P.J[c] = (float*)(base + L.off_fields + (6 + c) * fbytes);
+    }
+    float* maps[4];
+    for (int m = 0; m < 4; ++m) maps[m] = (float*)(base + L.off_maps + m * fbytes);
+    P.eps = maps[0]; P.sig = maps[1]; P.kap = maps[2]; P.mu = maps[3];
+    int pair = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            P.psiB[c][a] = nullptr;
+            P.psiE[c][a] = nullptr;
+            if (desc->bc[a].kind != TF_BC_CPML || c == a) continue;
+            P.psiB[c][a] = (float*)(base + L.off_psi + (2 * pair + 0) * fbytes);
+            P.psiE[c][a] = (float*)(base + L.off_psi + (2 * pair + 1) * fbytes);
+            ++pair;
+        }
+    size_t o = L.off_prof;
+    float* prof_host = (float*)malloc(sizeof(float) * 4 * (size_t)(L.N[0] + L.N[1] + L.N[2] + 3));
+    if (!prof_host) { delete h; return TF_ENOMEM; }
+    for (int a = 0; a < 3; ++a) {
+        const size_t pb = align_up(sizeof(float) * (size_t)L.N[a]);
+        float* d[4];
+        for (int m = 0; m < 4; ++m) d[m] = (float*)(base + o + m * pb);
+        o += 4 * pb;
+        P.pbE[a] = d[0]; P.pcE[a] = d[1]; P.pbB[a] = d[2]; P.pcB[a] = d[3];
+        float* hb = prof_host;
+        for (int p = 0; p < L.N[a]; ++p) {
+            if (desc->bc[a].kind == TF_BC_CPML) {
+                cpml_profile(desc, a, dt, (double)p, P.r[a], &hb[p], &hb[L.N[a] + p]);
+                cpml_profile(desc, a, dt, p + 0.5, P.r[a], &hb[2 * L.N[a] + p], &hb[3 * L.N[a] + p]);
+            } else {
+                hb[p] = hb[L.N[a] + p] = hb[2 * L.N[a] + p] = hb[3 * L.N[a] + p] = 0.f;
+            }
+        }
+        for (int m = 0; m < 4; ++m)
+            if (cudaMemcpyAsync(d[m], hb + m * L.N[a], sizeof(float) * L.N[a], cudaMemcpyHostToDevice,
+                                h->stream) != cudaSuccess) {
+                free(prof_host);
+                delete h;
+                return TF_ECUDA;
+            }
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) { free(prof_host); delete h; return TF_ECUDA; }
+    }
+    free(prof_host);
+    P.mur_save = desc->bc[2].kind == TF_BC_MUR ? (float*)(base + L.off_mur) : nullptr;
+    const size_t pbytes = align_up(sizeof(double) * TF_MAX_PROBES * TF_MAX_FREQS);
+    h->R.fdt = (const double*)(base + L.off_probe);
+    h->R.re = (double*)(base + L.off_probe + pbytes);
+    h->R.im = (double*)(base + L.off_probe + 2 * pbytes);
+    h->R.series = desc->series_capacity > 0 ? (double*)(base + L.off_series) : nullptr;
+    h->R.cap = desc->series_capacity;
+    h->R.dt = dt;
+    h->R.n = 0;
+    h->scratch = (float*)(base + L.off_scratch);
+    h->status = (unsigned*)(base + L.off_misc);
+    h->mm = h->status + 4;
+    h->fit_out = (double*)(base + L.off_misc + 64);
+    P.status = h->status;
+    // zero everything but the profiles, then vacuum materials
+    cudaError_t e = cudaMemsetAsync(base + L.off_fields, 0, L.off_prof - L.off_fields, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.off_mur, 0, L.off_misc + kAlign - L.off_mur, h->stream);
+    if (e == cudaSuccess)
+        e = launch_convert_materials(P, nullptr, nullptr, nullptr, nullptr, dt, maps[0], maps[1], maps[2],
+                                     maps[3], h->mm, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { delete h; return TF_ECUDA; }
+    *out = h;
+    return TF_OK;
+}
+
+tf_status tf_destroy(tf_handle h) {
+    if (!h) return TF_EINVAL;
+    cudaStreamSynchronize(h->stream);
+    delete h;
+    return TF_OK;
+}
+
+tf_status tf_storage_dims(tf_handle h, int dims[3]) {
+    if (!h || !dims) return TF_EINVAL;
+    for (int a = 0; a < 3; ++a) dims[a] = h->L.N[a];
+    return TF_OK;
+}
+
+tf_status tf_get_time(tf_handle h, int64_t* n, double* t) {
+    if (!h) return TF_EINVAL;
+    if (n) *n = h->level;
+    if (t) *t = h->level * h->dt;
+    return TF_OK;
+}
+
+tf_status tf_get_dt(tf_handle h, double* dt) {
+    if (!h || !dt) return TF_EINVAL;
+    *dt = h->dt;
+    return TF_OK;
+}
+
+tf_status tf_set_materials(tf_handle h, const float* eps_r, const float* mu_r, const float* lambda_L,
+                           const float* sigma, int on_device) {
+    if (!h) return TF_EINVAL;
+    if (h->level != 0 || h->primed) return TF_ESTATE;
+    const long long nc = h->L.ncell;
+    const float* src[4] = {eps_r, mu_r, lambda_L, sigma};
+    const float* dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int m = 0; m < 4; ++m) {
+        if (!src[m]) continue;
+        if (on_device) {
+            dev[m] = src[m];
+        } else {
+            float* st = h->scratch + m * nc;
+            TF_CUDA(cudaMemcpyAsync(st, src[m], sizeof(float) * nc, cudaMemcpyHostToDevice, h->stream));
+            dev[m] = st;
+        }
+    }
+    Params& P = h->P;
+    TF_CUDA(cudaMemsetAsync(h->mm, 0, 4 * sizeof(unsigned), h->stream));
+    TF_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    TF_CUDA(launch_convert_materials(P, dev[0], dev[1], dev[2], dev[3], h->dt, (float*)P.eps, (float*)P.sig,
+                                     (float*)P.kap, (float*)P.mu, h->mm, h->stream));
+    unsigned hm[4], st = 0;
+    TF_CUDA(cudaMemcpyAsync(hm, h->mm, sizeof(hm), cudaMemcpyDeviceToHost, h->stream));
+    TF_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    TF_CUDA(cudaStreamSynchronize(h->stream));
+    TF_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    P.uniform_mu = hm[2] ? 0 : 1;
+    if (st & kStatusBadMaterial) return TF_EINVAL;
+    float inv_eu, lon;
+    memcpy(&inv_eu, &hm[0], 4);
+    memcpy(&lon, &hm[1], 4);
+    const tf_grid_desc* d = &h->desc;
+    const double c2 = pow(kC0 * h->dt, 2) * (1.0 / (d->dx * d->dx) + 1.0 / (d->dy * d->dy) + 1.0 / (d->dz * d->dz));
+    if (c2 * inv_eu + lon > 1.0 + 1e-12) return TF_EUNSTABLE;
+    return TF_OK;
+}
+
+tf_status tf_set_field(tf_handle h, int comp, const float* src, int on_device) {
+    if (!h || !src || comp < 0 || comp > 8) return TF_EINVAL;
+    if (h->level != 0 || h->primed) return TF_ESTATE;
+    const float* dense = src;
+    if (!on_device) {
+        TF_CUDA(cudaMemcpyAsync(h->scratch, src, sizeof(float) * h->L.ndense, cudaMemcpyHostToDevice, h->stream));
+        dense = h->scratch;
+    }
+    float* dst = comp < 3 ? h->P.E[comp] : comp < 6 ? h->P.B[comp - 3] : h->P.J[comp - 6];
+    const double scale = comp < 3 ? 1.0 : comp < 6 ? kC0 : h->dt / kEps0;
+    TF_CUDA(launch_set_field(h->P, comp, dense, dst, scale, h->stream));
+    if (!on_device) TF_CUDA(cudaStreamSynchronize(h->stream));   // host buffer may be reused
+    return TF_OK;
+}
+
+tf_status tf_add_source(tf_handle h, int comp, const int lo[3], const int hi[3], double amp, int kind,
+                        double f, double t0, double tw, int* id) {
+    if (!h || !lo || !hi || comp < 0 || comp > 2 || kind < TF_SRC_GAUSS || kind > TF_SRC_GAUSS_SIN)
+        return TF_EINVAL;
+    if (h->nsrc >= TF_MAX_SOURCES) return TF_EINVAL;
+    if (kind != TF_SRC_SIN && !(tw > 0)) return TF_EINVAL;
+    SrcHost& s = h->src[h->nsrc];
+    s.comp = comp;
+    for (int a = 0; a < 3; ++a) {
+        s.lo[a] = lo[a] < 0 ? 0 : lo[a];
+        s.hi[a] = hi[a] > h->L.N[a] ? h->L.N[a] : hi[a];
+    }
+    s.kind = kind; s.amp = amp; s.f = f; s.t0 = t0; s.tw = tw;
+    if (id) *id = h->nsrc;
+    h->nsrc++;
+    return TF_OK;
+}
+
+tf_status tf_add_probe(tf_handle h, int comp, const int p[3], const double* freqs, int nfreq, int64_t n0,
+                       int* id) {
+    if (!h || !p || comp < 0 || comp > 2 || nfreq < 0 || nfreq > TF_MAX_FREQS || (nfreq && !freqs))
+        return TF_EINVAL;
+    if (h->R.n >= h->desc.max_probes) return TF_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (p[a] < 0 || p[a] >= h->L.N[a]) return TF_EINVAL;
+    const int k = h->R.n;
+    double fdt[TF_MAX_FREQS] = {0};
+    for (int f = 0; f < nfreq; ++f) {
+        h->freqs[k][f] = freqs[f];
+        fdt[f] = freqs[f] * h->dt;
+    }
+    TF_CUDA(cudaMemcpyAsync((double*)h->R.fdt + k * TF_MAX_FREQS, fdt, sizeof(fdt), cudaMemcpyHostToDevice,
+                            h->stream));
+    TF_CUDA(cudaStreamSynchronize(h->stream));
+    h->R.nfreq[k] = nfreq;
+    h->R.comp[k] = comp;
+    h->R.q[k] = lin(h->P, p[0], p[1], p[2]);
+    h->R.n0[k] = n0;
+    h->R.n++;
+    if (id) *id = k;
+    return TF_OK;
+}
+
+namespace {
+
+// per-step launch sequence; with `ev` non-null an event is recorded before the
+// step and after each launch, ev[0..4] for probe, B, E, Mur
+cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
+    cudaStream_t st = h->stream;
+    cudaError_t e = cudaSuccess;
+    if (ev) cudaEventRecord(ev[0], st);
+    if (h->R.n) e = launch_probe(h->P, h->R, h->level, st);
+    if (ev) cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = launch_update_B(h->P, st);
+    if (ev) cudaEventRecord(ev[2], st);
+    const double t1 = (double)(h->level + 1) * h->dt;
+    for (int q = 0; q < h->nsrc; ++q) S.amp[q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
+    if (e == cudaSuccess) e = launch_update_E(h->P, S, st);
+    if (ev) cudaEventRecord(ev[3], st);
+    if (e == cudaSuccess && h->desc.bc[2].kind == TF_BC_MUR) e = launch_mur(h->P, st);
+    if (ev) cudaEventRecord(ev[4], st);
+    h->level++;
+    return e;
+}
+
+void fill_sources(const tf_ctx* h, Sources& S) {
+    S.n = h->nsrc;
+    for (int a = 0; a < 3; ++a) { S.bb_lo[a] = 1 << 30; S.bb_hi[a] = -1; }
+    for (int s = 0; s < h->nsrc; ++s) {
+        S.comp[s] = h->src[s].comp;
+        S.amp[s] = 0.f;
+        for (int a = 0; a < 3; ++a) {
+            S.lo[s][a] = h->src[s].lo[a];
+            S.hi[s][a] = h->src[s].hi[a];
+            if (S.lo[s][a] < S.bb_lo[a]) S.bb_lo[a] = S.lo[s][a];
+            if (S.hi[s][a] > S.bb_hi[a]) S.bb_hi[a] = S.hi[s][a];
+        }
+    }
+}
+
+}  // namespace
+
+tf_status tf_step(tf_handle h, int64_t nsteps) {
+    if (!h || nsteps < 0) return TF_EINVAL;
+    if (nsteps == 0) return TF_OK;
+    if (!h->primed) {
+        TF_CUDA(launch_prime(h->P, h->stream));
+        h->primed = 1;
+    }
+    Sources S;
+    fill_sources(h, S);
+    for (int64_t s = 0; s < nsteps; ++s) TF_CUDA(launch_one_step(h, S, nullptr));
+    return TF_OK;
+}
+
+tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds) {
+    if (!h || nsteps < 0 || !kernel_ms || !launches || nkinds < 1 || nkinds > 4) return TF_EINVAL;
+    for (int k = 0; k < nkinds; ++k) { kernel_ms[k] = 0.0; launches[k] = 0; }
+    if (nsteps == 0) return TF_OK;
+    if (!h->primed) {
+        TF_CUDA(launch_prime(h->P, h->stream));
+        h->primed = 1;
+    }
+    constexpr int kRing = 64;
+    cudaEvent_t ev[kRing][5];
+    int created = 0;
+    tf_status rc = TF_OK;
+    for (; created < kRing; ++created) {
+        bool ok = true;
+        for (int m = 0; m < 5; ++m)
+            if (cudaEventCreate(&ev[created][m]) != cudaSuccess) ok = false;
+        if (!ok) { rc = TF_ECUDA; ++created; break; }
+    }
+    const int has[4] = {h->R.n > 0, 1, 1, h->desc.bc[2].kind == TF_BC_MUR};
+    Sources S;
+    fill_sources(h, S);
+    int64_t done = 0;
+    while (rc == TF_OK && done < nsteps) {
+        const int m = (int)((nsteps - done) < kRing ? (nsteps - done) : kRing);
+        for (int s = 0; s < m && rc == TF_OK; ++s)
+            if (launch_one_step(h, S, ev[s]) != cudaSuccess) rc = TF_ECUDA;
+        if (rc != TF_OK || cudaStreamSynchronize(h->stream) != cudaSuccess) { rc = TF_ECUDA; break; }
+        for (int s = 0; s < m; ++s)
+            for (int k = 0; k < nkinds; ++k) {
+                if (!has[k]) continue;
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, ev[s][k], ev[s][k + 1]) != cudaSuccess) { rc = TF_ECUDA; break; }
+                kernel_ms[k] += ms;
+                launches[k] += 1;
+            }
+        done += m;
+    }
+    for (int s = 0; s < created && s < kRing; ++s)
+        for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[s][k]);
+    for (int k = 0; k < nkinds; ++k)
+        if (launches[k]) kernel_ms[k] /= (double)launches[k];
+    return rc;
+}
+
+tf_status tf_sync(tf_handle h) {
+    if (!h) return TF_EINVAL;
+    unsigned st = 0;
+    TF_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    TF_CUDA(cudaStreamSynchronize(h->stream));
+    if (st & kStatusTimeout) return TF_ETIMEOUT;
+    if (st & kStatusNonFinite) return TF_ENONFINITE;
+    return TF_OK;
+}
+
+tf_status tf_read_probe_dft(tf_handle h, int id, double* re, double* im) {
+    if (!h || id < 0 || id >= h->R.n || !re || !im) return TF_EINVAL;
+    const int nf = h->R.nfreq[id];
+    TF_CUDA(cudaMemcpyAsync(re, h->R.re + id * TF_MAX_FREQS, sizeof(double) * nf, cudaMemcpyDeviceToHost, h->stream));
+    TF_CUDA(cudaMemcpyAsync(im, h->R.im + id * TF_MAX_FREQS, sizeof(double) * nf, cudaMemcpyDeviceToHost, h->stream));
+    TF_CUDA(cudaStreamSynchronize(h->stream));
+    return TF_OK;
+}
+
+tf_status tf_read_probe_series(tf_handle h, int id, double* out, int64_t n) {
+    if (!h || id < 0 || id >= h->R.n || !out || n < 0) return TF_EINVAL;
+    if (n > h->R.cap || n > h->level) return TF_EINVAL;
+    if (n == 0) return TF_OK;
+    TF_CUDA(cudaMemcpyAsync(out, h->R.series + (long long)id * h->R.cap, sizeof(double) * n,
+                            cudaMemcpyDeviceToHost, h->stream));
+    TF_CUDA(cudaStreamSynchronize(h->stream));
+    return TF_OK;
+}
+
+tf_status tf_read_field(tf_handle h, int comp, float* dst, int on_device) {
+    if (!h || !dst || comp < 0 || comp > 8) return TF_EINVAL;
+    float* out = on_device ? dst : h->scratch;
+    const double scale = comp < 3 ? 1.0 : comp < 6 ? 1.0 / kC0 : kEps0 / h->dt;
+    TF_CUDA(launch_read_field(h->P, comp, h->primed, out, scale, h->stream));
+    if (!on_device)
+        TF_CUDA(cudaMemcpyAsync(dst, out, sizeof(float) * h->L.ndense, cudaMemcpyDeviceToHost, h->stream));
+    TF_CUDA(cudaStreamSynchronize(h->stream));
+    return TF_OK;
+}
+
+tf_status tf_fit_q(tf_handle h, int id, double f_guess, double q_guess, double* f0, double* alpha, double* q) {
+    if (!h || id < 0 || id >= h->R.n) return TF_EINVAL;
+    if (h->R.nfreq[id] < 4 || !(q_guess > 0)) return TF_EINVAL;
+    if (h->level <= h->R.n0[id]) return TF_ESTATE;
+    TF_CUDA(launch_fit_q(h->R.re + id * TF_MAX_FREQS, h->R.im + id * TF_MAX_FREQS,
+                         h->R.fdt + id * TF_MAX_FREQS, h->R.nfreq[id], h->dt, h->R.n0[id], h->level, f_guess,
+                         q_guess, h->fit_out, h->stream));
+    double o[4];
+    TF_CUDA(cudaMemcpyAsync(o, h->fit_out, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+    TF_CUDA(cudaStreamSynchronize(h->stream));
+    if (!(o[3] > 0)) return TF_ENOTSUP;   // fit did not converge
+    if (f0) *f0 = o[0];
+    if (alpha) *alpha = o[1];
+    if (q) *q = o[2];
+    return TF_OK;
+}
+
+}  // extern "C"

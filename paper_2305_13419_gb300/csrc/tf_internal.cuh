@@ -1,0 +1,207 @@
+// tf_internal.cuh -- device-side layout and helpers of the two-fluid Yee
+// library (arXiv 2305.13419, Sec. 3 / Algorithm 1).
+//
+// Units on the GPU (all FP32, all O(1) for O(1) V/m fields):
+//   E                 [V/m]
+//   Bt = c0 B         [V/m]
+//   Jt = (dt/eps0) Js [V/m]
+//   r_a = c0 dt / d_a (dimensionless)
+// so that the fused leapfrog reads
+//   Bt^{n+1/2} = Bt^{n-1/2} - sum_a s (r_a D_a E^n + psiB)                   (steps 5+1)
+//   Jt^{n+1/2} = Jt^{n-1/2} + kt_e E^n,  kt = (c0 dt)^2 / (lambda^2 mu_r)      (steps 4+2)
+//   E^{n+1}    = ca E^n + cb ( sum_a s (r_a D_a (Bt/mu_r) + psiE) - Jt^{n+1/2} ) (step 3)
+//   ca = (eps_e - (1-theta) st_e) / (eps_e + theta st_e),  cb = 1 / (eps_e + theta st_e),
+//   st = sigma dt / eps0.
+// Per-cell maps are stored scaled (eps_r, st, kt, mu_r) on the same padded
+// storage grid as the fields; edge and face values are formed in-kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "twofluid.h"
+
+namespace tf {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kMu0 = 1.25663706212e-6;
+constexpr double kEps0 = 8.8541878128e-12;
+
+// status bits latched on the device
+constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusBadMaterial = 2u;
+constexpr unsigned kStatusTimeout = 4u;
+
+struct Params {
+    int N[3];            // storage points per axis
+    int n[3];            // cells per axis
+    int per[3];          // periodic flag per axis
+    int bc[3];           // TF_BC_* per axis
+    int L[3];            // CPML cells per axis (0 without CPML)
+    int pitch;           // floats per x row (multiple of 32)
+    long long plane;     // floats per z plane
+    float r[3];          // c0 dt / d_a
+    float theta;
+    int edge_rule;
+    int uniform_mu;      // all mu_r == 1: skip the mu map
+    float mur_M;         // (c0 dt - dz) / (c0 dt + dz)
+    float* E[3];
+    float* B[3];
+    float* J[3];
+    const float* eps;    // eps_r per cell
+    const float* sig;    // sigma dt / eps0 per cell
+    const float* kap;    // (c0 dt)^2 / (lambda^2 mu_r) per cell
+    const float* mu;     // mu_r per cell
+    float* psiB[3][3];   // [component][derivative axis], nullptr if absent
+    float* psiE[3][3];
+    const float* pbE[3]; // CPML b at integer positions along axis a
+    const float* pcE[3]; // CPML c * r_a at integer positions
+    const float* pbB[3]; // ... at half-integer positions
+    const float* pcB[3];
+    float* mur_save;     // [wall 2][comp 2][plane]: E^n on the planes next to the Mur walls
+    unsigned* status;
+};
+
+struct Sources {
+    int n;
+    int comp[TF_MAX_SOURCES];
+    int lo[TF_MAX_SOURCES][3];
+    int hi[TF_MAX_SOURCES][3];
+    float amp[TF_MAX_SOURCES];  // amp * s(t^{n+1}) of this step
+    int bb_lo[3], bb_hi[3];     // bounding box of all sources
+};
+
+struct Probes {
+    int n;
+    int nfreq[TF_MAX_PROBES];
+    int comp[TF_MAX_PROBES];
+    long long q[TF_MAX_PROBES];     // padded linear index of the probe point
+    long long n0[TF_MAX_PROBES];
+    const double* fdt;              // [probe][TF_MAX_FREQS]: f_k dt
+    double* re;                     // [probe][TF_MAX_FREQS]
+    double* im;
+    double* series;                 // [probe][cap]
+    long long cap;
+    double dt;
+};
+
+__host__ __device__ __forceinline__ long long lin(const Params& P, int i, int j, int k) {
+    return (long long)k * P.plane + (long long)j * P.pitch + i;
+}
+__device__ __forceinline__ int nxt(const Params& P, int a, int p) {
+    return (p + 1 < P.N[a]) ? p + 1 : (P.per[a] ? 0 : p);
+}
+__device__ __forceinline__ int prv(const Params& P, int a, int p) {
+    return (p > 0) ? p - 1 : (P.per[a] ? P.N[a] - 1 : p);
+}
+// +1 when axis a follows component c cyclically, -1 otherwise (curl sign)
+__host__ __device__ __forceinline__ float curl_sign(int c, int a) {
+    return ((a - c + 3) % 3 == 1) ? 1.f : -1.f;
+}
+
+// E_c at point p is advanced by the curl (not outside, not on a wall)
+__device__ __forceinline__ bool upd_E(const Params& P, int c, const int p[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (P.per[a]) continue;
+        if (a == c) {
+            if (p[a] >= P.n[a]) return false;
+        } else if (p[a] < 1 || p[a] > P.n[a] - 1) {
+            return false;
+        }
+    }
+    return true;
+}
+// B_c at point p is advanced (normal B on a wall is not)
+__device__ __forceinline__ bool upd_B(const Params& P, int c, const int p[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (P.per[a]) continue;
+        if (a != c) {
+            if (p[a] >= P.n[a]) return false;
+        } else if (p[a] < 1 || p[a] > P.n[a] - 1) {
+            return false;
+        }
+    }
+    return true;
+}
+// tangential E on a Mur z wall (z = 0 or z = nz), interior along x and y
+__device__ __forceinline__ bool mur_E(const Params& P, int c, const int p[3]) {
+    if (P.bc[2] != TF_BC_MUR || c > 1) return false;
+    if (p[2] != 0 && p[2] != P.n[2]) return false;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        if (P.per[a]) continue;
+        if (a == c) {
+            if (p[a] >= P.n[a]) return false;
+        } else if (p[a] < 1 || p[a] > P.n[a] - 1) {
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ bool in_slab(const Params& P, int a, int p) {
+    return P.L[a] > 0 && (p < P.L[a] || p >= P.n[a] - P.L[a]);
+}
+
+// edge material of E_c at p: eps (mean of 4 cells), st and kt per edge rule
+__device__ __forceinline__ void edge_material(const Params& P, int c, const int p[3], float& eps,
+                                              float& st, float& kt) {
+    const int b1 = (c + 1) % 3, b2 = (c + 2) % 3;
+    float se = 0.f, ss = 0.f, sk = 0.f;
+    int ns = 0, nk = 0;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            int cc[3];
+            cc[c] = p[c];
+            cc[b1] = u ? prv(P, b1, p[b1]) : p[b1];
+            cc[b2] = v ? prv(P, b2, p[b2]) : p[b2];
+            const long long m = lin(P, cc[0], cc[1], cc[2]);
+            const float e = __ldg(P.eps + m), s = __ldg(P.sig + m), k = __ldg(P.kap + m);
+            se += e;
+            ss += s;
+            sk += k;
+            ns += s > 0.f;
+            nk += k > 0.f;
+        }
+    eps = 0.25f * se;
+    if (P.edge_rule == TF_EDGE_PLAIN_MEAN) {
+        st = 0.25f * ss;
+        kt = 0.25f * sk;
+    } else {
+        st = ns ? ss / (float)ns : 0.f;
+        kt = nk ? sk / (float)nk : 0.f;
+    }
+}
+
+// 1 / mu_f of face B_c at p (mean mu_r of the two cells across the face)
+__device__ __forceinline__ float inv_mu_face(const Params& P, int c, const int p[3]) {
+    if (P.uniform_mu) return 1.f;
+    int q[3] = {p[0], p[1], p[2]};
+    q[c] = prv(P, c, p[c]);
+    const float m0 = __ldg(P.mu + lin(P, p[0], p[1], p[2]));
+    const float m1 = __ldg(P.mu + lin(P, q[0], q[1], q[2]));
+    return 2.f / (m0 + m1);
+}
+
+// launchers (tf_kernels.cu)
+cudaError_t launch_convert_materials(const Params& P, const float* eps_r, const float* mu_r,
+                                     const float* lam, const float* sigma, double dt,
+                                     float* eps, float* sig, float* kap, float* mu,
+                                     unsigned* minmax, cudaStream_t st);
+cudaError_t launch_set_field(const Params& P, int comp, const float* dense, float* dst, double scale,
+                             cudaStream_t st);
+cudaError_t launch_prime(const Params& P, cudaStream_t st);
+cudaError_t launch_read_field(const Params& P, int comp, int primed, float* dense, double scale,
+                              cudaStream_t st);
+cudaError_t launch_probe(const Params& P, const Probes& R, long long n, cudaStream_t st);
+cudaError_t launch_update_B(const Params& P, cudaStream_t st);
+cudaError_t launch_update_E(const Params& P, const Sources& S, cudaStream_t st);
+cudaError_t launch_mur(const Params& P, cudaStream_t st);
+cudaError_t launch_fit_q(const double* re, const double* im, const double* fdt, int nfreq,
+                         double dt, long long n0, long long N, double f_guess, double q_guess,
+                         double* out, cudaStream_t st);
+
+}  // namespace tf
