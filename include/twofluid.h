@@ -155,9 +155,11 @@ tf_status tf_add_probe(tf_handle h, int comp, const int p[3], const double* freq
                        int64_t n0, int* id);
 
 /* Advance nsteps >= 0 steps of Algorithm 1 (fused form) on the stream:
- * probe sample, B update with CPML memory, Js update, theta-scheme E update
- * with sources, Mur walls.  Asynchronous; errors of the launches are
- * returned, device-side errors latch for tf_sync(). */
+ * per step one probe-DFT launch and one fused launch doing the B update with
+ * CPML memory, the Js update, the theta-scheme E update with sources, the
+ * Mur walls and the non-finite watchdog.  Asynchronous; launch errors are
+ * returned (the handle is then unusable), device-side errors latch for
+ * tf_sync(). */
 tf_status tf_step(tf_handle h, int64_t nsteps);
 
 /* tf_step with per-kernel timing (the library's profiling hook): advances
@@ -165,7 +167,7 @@ tf_status tf_step(tf_handle h, int64_t nsteps);
  * stream around every kernel it launches.  On return (the stream is
  * synchronised) kernel_ms[k] is the mean duration in ms of one launch of
  * kernel kind k and launches[k] the number of launches, for k = 0 probe DFT,
- * 1 B update, 2 E update, 3 Mur walls (arrays of nkinds <= 4 entries). */
+ * 1 fused step (arrays of nkinds <= 2 entries). */
 tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds);
 
 /* Wait for the stream and return the latched device status

@@ -22,8 +22,9 @@ struct Layout {
     long long total;        // floats per field array (padded)
     long long ncell, ndense;
     int ncpml_pairs;        // (component, axis) pairs carrying psi
-    size_t off_fields, off_maps, off_psi, off_prof, off_mur, off_probe, off_series, off_scratch,
-        off_misc, bytes;
+    int ntx, nty, nch, kend; // fused-step tiles, z chunks, planes iterated
+    size_t off_fields, off_maps, off_psi, off_prof, off_zero, off_probe, off_series, off_scratch,
+        off_tiles, off_misc, bytes;
     long long scratch_floats;
 };
 
@@ -67,18 +68,23 @@ Layout layout_of(const tf_grid_desc* d) {
     L.ncpml_pairs = 0;
     for (int a = 0; a < 3; ++a)
         if (d->bc[a].kind == TF_BC_CPML) L.ncpml_pairs += 2;
+    L.ntx = (L.N[0] + kSX - 1) / kSX;
+    L.nty = (L.N[1] + kSY - 1) / kSY;
+    L.kend = d->bc[2].kind == TF_BC_PERIODIC ? L.N[2] : L.N[2] - 1;
+    L.nch = (L.kend + kChunk - 1) / kChunk;
     const size_t fbytes = align_up(sizeof(float) * (size_t)L.total);
     size_t o = 0;
-    L.off_fields = o; o += 9 * fbytes;
+    L.off_fields = o; o += 15 * fbytes;   // E, B (two buffers each), Js
     L.off_maps = o;   o += 4 * fbytes;
-    L.off_psi = o;    o += 2 * (size_t)L.ncpml_pairs * fbytes;
+    L.off_psi = o;    o += 3 * (size_t)L.ncpml_pairs * fbytes;   // psi_B (two buffers), psi_E
     L.off_prof = o;
     for (int a = 0; a < 3; ++a) o += 4 * align_up(sizeof(float) * (size_t)L.N[a]);
-    L.off_mur = o;    o += (d->bc[2].kind == TF_BC_MUR) ? 4 * align_up(sizeof(float) * (size_t)L.pitch * L.N[1]) : 0;
+    L.off_zero = o;
     L.off_probe = o;  o += 3 * align_up(sizeof(double) * TF_MAX_PROBES * TF_MAX_FREQS);
     L.off_series = o; o += align_up(sizeof(double) * (size_t)d->max_probes * (size_t)d->series_capacity);
     L.scratch_floats = 4 * L.ncell > L.ndense ? 4 * L.ncell : L.ndense;
     L.off_scratch = o; o += align_up(sizeof(float) * (size_t)L.scratch_floats);
+    L.off_tiles = o;  o += align_up(sizeof(float4) * (size_t)L.ntx * L.nty * L.N[2]);
     L.off_misc = o;   o += kAlign;
     L.bytes = o;
     return L;
@@ -105,6 +111,8 @@ struct tf_ctx {
     tf_grid_desc desc;
     Layout L;
     Params P;
+    StepOut O;
+    int step_blocks;
     Probes R;
     cudaStream_t stream;
     double dt;
@@ -202,10 +210,13 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
     P.mur_M = (float)((kC0 * dt - desc->dz) / (kC0 * dt + desc->dz));
     const size_t fbytes = align_up(sizeof(float) * (size_t)L.total);
     char* base = h->ws;
+    StepOut& O = h->O;
     for (int c = 0; c < 3; ++c) {
         P.E[c] = (float*)(base + L.off_fields + (0 + c) * fbytes);
         P.B[c] = (float*)(base + L.off_fields + (3 + c) * fbytes);
         P.J[c] = (float*)(base + L.off_fields + (6 + c) * fbytes);
+        O.E[c] = (float*)(base + L.off_fields + (9 + c) * fbytes);
+        O.B[c] = (float*)(base + L.off_fields + (12 + c) * fbytes);
     }
     float* maps[4];
     for (int m = 0; m < 4; ++m) maps[m] = (float*)(base + L.off_maps + m * fbytes);
@@ -215,11 +226,19 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
         for (int c = 0; c < 3; ++c) {
             P.psiB[c][a] = nullptr;
             P.psiE[c][a] = nullptr;
+            O.psiB[c][a] = nullptr;
             if (desc->bc[a].kind != TF_BC_CPML || c == a) continue;
-            P.psiB[c][a] = (float*)(base + L.off_psi + (2 * pair + 0) * fbytes);
-            P.psiE[c][a] = (float*)(base + L.off_psi + (2 * pair + 1) * fbytes);
+            P.psiB[c][a] = (float*)(base + L.off_psi + (3 * pair + 0) * fbytes);
+            O.psiB[c][a] = (float*)(base + L.off_psi + (3 * pair + 1) * fbytes);
+            P.psiE[c][a] = (float*)(base + L.off_psi + (3 * pair + 2) * fbytes);
             ++pair;
         }
+    O.tilemat = (const float4*)(base + L.off_tiles);
+    O.ntx = L.ntx;
+    O.nty = L.nty;
+    O.nch = L.nch;
+    O.kend = L.kend;
+    O.base = 0;
     size_t o = L.off_prof;
     float* prof_host = (float*)malloc(sizeof(float) * 4 * (size_t)(L.N[0] + L.N[1] + L.N[2] + 3));
     if (!prof_host) { delete h; return TF_ENOMEM; }
@@ -248,7 +267,6 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
         if (cudaStreamSynchronize(h->stream) != cudaSuccess) { free(prof_host); delete h; return TF_ECUDA; }
     }
     free(prof_host);
-    P.mur_save = desc->bc[2].kind == TF_BC_MUR ? (float*)(base + L.off_mur) : nullptr;
     const size_t pbytes = align_up(sizeof(double) * TF_MAX_PROBES * TF_MAX_FREQS);
     h->R.fdt = (const double*)(base + L.off_probe);
     h->R.re = (double*)(base + L.off_probe + pbytes);
@@ -261,13 +279,26 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
     h->status = (unsigned*)(base + L.off_misc);
     h->mm = h->status + 4;
     h->fit_out = (double*)(base + L.off_misc + 64);
+    O.ctr = (unsigned long long*)(base + L.off_misc + 128);
     P.status = h->status;
+    {
+        int dev = 0, sms = 1;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            delete h;
+            return TF_ECUDA;
+        }
+        const long long items = (long long)L.ntx * L.nty * L.nch;
+        long long nb = (long long)sms * step_blocks_per_sm();
+        h->step_blocks = (int)(nb < items ? nb : items);
+    }
     // zero everything but the profiles, then vacuum materials
     cudaError_t e = cudaMemsetAsync(base + L.off_fields, 0, L.off_prof - L.off_fields, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.off_mur, 0, L.off_misc + kAlign - L.off_mur, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + L.off_zero, 0, L.off_misc + kAlign - L.off_zero, h->stream);
     if (e == cudaSuccess)
         e = launch_convert_materials(P, nullptr, nullptr, nullptr, nullptr, dt, maps[0], maps[1], maps[2],
                                      maps[3], h->mm, h->stream);
+    if (e == cudaSuccess) e = launch_tile_materials(P, (float4*)O.tilemat, L.ntx, L.nty, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) { delete h; return TF_ECUDA; }
     *out = h;
@@ -322,6 +353,7 @@ tf_status tf_set_materials(tf_handle h, const float* eps_r, const float* mu_r, c
     TF_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
     TF_CUDA(launch_convert_materials(P, dev[0], dev[1], dev[2], dev[3], h->dt, (float*)P.eps, (float*)P.sig,
                                      (float*)P.kap, (float*)P.mu, h->mm, h->stream));
+    TF_CUDA(launch_tile_materials(P, (float4*)h->O.tilemat, h->L.ntx, h->L.nty, h->stream));
     unsigned hm[4], st = 0;
     TF_CUDA(cudaMemcpyAsync(hm, h->mm, sizeof(hm), cudaMemcpyDeviceToHost, h->stream));
     TF_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
@@ -398,22 +430,25 @@ tf_status tf_add_probe(tf_handle h, int comp, const int p[3], const double* freq
 
 namespace {
 
-// per-step launch sequence; with `ev` non-null an event is recorded before the
-// step and after each launch, ev[0..4] for probe, B, E, Mur
+// per-step launch sequence (probe DFT of E^n, fused step, buffer swap); with
+// `ev` non-null an event is recorded before, between and after the launches
 cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
     cudaStream_t st = h->stream;
     cudaError_t e = cudaSuccess;
     if (ev) cudaEventRecord(ev[0], st);
     if (h->R.n) e = launch_probe(h->P, h->R, h->level, st);
     if (ev) cudaEventRecord(ev[1], st);
-    if (e == cudaSuccess) e = launch_update_B(h->P, st);
-    if (ev) cudaEventRecord(ev[2], st);
     const double t1 = (double)(h->level + 1) * h->dt;
     for (int q = 0; q < h->nsrc; ++q) S.amp[q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
-    if (e == cudaSuccess) e = launch_update_E(h->P, S, st);
-    if (ev) cudaEventRecord(ev[3], st);
-    if (e == cudaSuccess && h->desc.bc[2].kind == TF_BC_MUR) e = launch_mur(h->P, st);
-    if (ev) cudaEventRecord(ev[4], st);
+    if (e == cudaSuccess) e = launch_step(h->P, h->O, S, h->step_blocks, st);
+    if (ev) cudaEventRecord(ev[2], st);
+    // the new state is in O's buffers: swap
+    for (int c = 0; c < 3; ++c) {
+        float* t = h->P.E[c]; h->P.E[c] = h->O.E[c]; h->O.E[c] = t;
+        t = h->P.B[c]; h->P.B[c] = h->O.B[c]; h->O.B[c] = t;
+        for (int a = 0; a < 3; ++a) { t = h->P.psiB[c][a]; h->P.psiB[c][a] = h->O.psiB[c][a]; h->O.psiB[c][a] = t; }
+    }
+    h->O.base += (unsigned long long)h->L.ntx * h->L.nty * h->L.nch + (unsigned long long)h->step_blocks;
     h->level++;
     return e;
 }
@@ -449,7 +484,7 @@ tf_status tf_step(tf_handle h, int64_t nsteps) {
 }
 
 tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds) {
-    if (!h || nsteps < 0 || !kernel_ms || !launches || nkinds < 1 || nkinds > 4) return TF_EINVAL;
+    if (!h || nsteps < 0 || !kernel_ms || !launches || nkinds < 1 || nkinds > 2) return TF_EINVAL;
     for (int k = 0; k < nkinds; ++k) { kernel_ms[k] = 0.0; launches[k] = 0; }
     if (nsteps == 0) return TF_OK;
     if (!h->primed) {
@@ -457,16 +492,16 @@ tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t*
         h->primed = 1;
     }
     constexpr int kRing = 64;
-    cudaEvent_t ev[kRing][5];
+    cudaEvent_t ev[kRing][3];
     int created = 0;
     tf_status rc = TF_OK;
     for (; created < kRing; ++created) {
         bool ok = true;
-        for (int m = 0; m < 5; ++m)
+        for (int m = 0; m < 3; ++m)
             if (cudaEventCreate(&ev[created][m]) != cudaSuccess) ok = false;
         if (!ok) { rc = TF_ECUDA; ++created; break; }
     }
-    const int has[4] = {h->R.n > 0, 1, 1, h->desc.bc[2].kind == TF_BC_MUR};
+    const int has[2] = {h->R.n > 0, 1};
     Sources S;
     fill_sources(h, S);
     int64_t done = 0;
@@ -486,7 +521,7 @@ tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t*
         done += m;
     }
     for (int s = 0; s < created && s < kRing; ++s)
-        for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[s][k]);
+        for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[s][k]);
     for (int k = 0; k < nkinds; ++k)
         if (launches[k]) kernel_ms[k] /= (double)launches[k];
     return rc;

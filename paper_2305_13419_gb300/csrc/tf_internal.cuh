@@ -58,8 +58,25 @@ struct Params {
     const float* pcE[3]; // CPML c * r_a at integer positions
     const float* pbB[3]; // ... at half-integer positions
     const float* pcB[3];
-    float* mur_save;     // [wall 2][comp 2][plane]: E^n on the planes next to the Mur walls
     unsigned* status;
+};
+
+// Fused step (tf_step.cu): the state ping-pongs between two buffers each
+// step; the kernel reads Params' buffers and writes these.
+constexpr int kTX = 32, kTY = 8;             // threads per tile (x, y)
+constexpr int kSX = kTX - 1, kSY = kTY - 1;  // owned columns per tile (one halo column / row)
+constexpr int kChunk = 16;                   // z planes per work item
+
+struct StepOut {
+    float* E[3];
+    float* B[3];
+    float* psiB[3][3];
+    const float4* tilemat;   // per (tile, plane): {ca, cb, cj, 1/mu} of a uniform-material
+                             // tile-plane, ca = NaN where the material varies
+    int ntx, nty, nch;       // tiles along x, y; z chunks
+    int kend;                // planes iterated: N2 (periodic z) or N2 - 1
+    unsigned long long* ctr; // work counter (monotone across launches)
+    unsigned long long base; // counter value at the start of this launch
 };
 
 struct Sources {
@@ -197,9 +214,9 @@ cudaError_t launch_prime(const Params& P, cudaStream_t st);
 cudaError_t launch_read_field(const Params& P, int comp, int primed, float* dense, double scale,
                               cudaStream_t st);
 cudaError_t launch_probe(const Params& P, const Probes& R, long long n, cudaStream_t st);
-cudaError_t launch_update_B(const Params& P, cudaStream_t st);
-cudaError_t launch_update_E(const Params& P, const Sources& S, cudaStream_t st);
-cudaError_t launch_mur(const Params& P, cudaStream_t st);
+cudaError_t launch_step(const Params& P, const StepOut& O, const Sources& S, int blocks, cudaStream_t st);
+cudaError_t launch_tile_materials(const Params& P, float4* tilemat, int ntx, int nty, cudaStream_t st);
+int step_blocks_per_sm();
 cudaError_t launch_fit_q(const double* re, const double* im, const double* fdt, int nfreq,
                          double dt, long long n0, long long N, double f_guess, double q_guess,
                          double* out, cudaStream_t st);

@@ -1,12 +1,7 @@
 // tf_kernels.cu -- CUDA kernels of the two-fluid Yee library for sm_103a.
 //
-// One time step of Algorithm 1 (arXiv 2305.13419, Sec. 3) in its fused
-// leapfrog form:
+// The per-step kernels besides the fused step of tf_step.cu:
 //   k_probe     running FP64 DFT of E^n at the probe points (Secs. 4.2, 5)
-//   k_update_B  CPML memory psi_B and Bt^{n+1/2} from curl E^n (steps 5 + 1)
-//   k_update_E  Js^{n+1/2} (steps 4 + 2), CPML psi_E and the theta-scheme
-//               E^{n+1} (step 3), soft sources, non-finite watchdog
-//   k_mur       first-order Mur on the z walls
 // plus set-up and read-back kernels (material scaling, level-0 priming
 // B^{-1/2} = B^0 + dt/2 curl E^0 and Js^{-1/2} = Js^0 - dt/2 kappa E^0, and
 // integer-level read-back B^n = B^{n-1/2} - dt/2 curl E^n,
@@ -151,11 +146,11 @@ __global__ void k_read_field(Params P, int comp, int primed, float* dense, doubl
         v = b;
     } else {
         const int c = comp - 6;
-        float jt = P.J[c][q];
-        if (primed && upd_E(P, c, p)) {
+        float jt = 0.f;   // Js lives on superconducting edges only
+        if (upd_E(P, c, p)) {
             float eps, st, kt;
             edge_material(P, c, p, eps, st, kt);
-            if (kt > 0.f) jt += 0.5f * kt * P.E[c][q];
+            if (kt > 0.f) jt = P.J[c][q] + (primed ? 0.5f * kt * P.E[c][q] : 0.f);
         }
         v = jt;
     }
@@ -175,115 +170,6 @@ __global__ void k_probe(Params P, Probes R, long long n) {
         sincospi(2.0 * ph, &sn, &cs);
         R.re[pr * TF_MAX_FREQS + f] += s * cs * R.dt;
         R.im[pr * TF_MAX_FREQS + f] -= s * sn * R.dt;
-    }
-}
-
-__global__ void __launch_bounds__(BX* BY* BZ) k_update_B(Params P) {
-    int i, j, k;
-    if (!point_of(P, i, j, k)) return;
-    const int p[3] = {i, j, k};
-    const long long q = lin(P, i, j, k);
-    if (P.bc[2] == TF_BC_MUR) {   // keep E^n next to the walls for the Mur update
-        const long long o = (long long)j * P.pitch + i;
-        if (k == 1) {
-            P.mur_save[0 * P.plane + o] = P.E[0][q];
-            P.mur_save[1 * P.plane + o] = P.E[1][q];
-        }
-        if (k == P.n[2] - 1) {
-            P.mur_save[2 * P.plane + o] = P.E[0][q];
-            P.mur_save[3 * P.plane + o] = P.E[1][q];
-        }
-    }
-#pragma unroll
-    for (int cb = 0; cb < 3; ++cb) {
-        if (!upd_B(P, cb, p)) continue;
-        float acc = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (a == cb) continue;
-            const int e = 3 - cb - a;
-            int pn[3] = {i, j, k};
-            pn[a] = nxt(P, a, p[a]);
-            const float dE = P.E[e][lin(P, pn[0], pn[1], pn[2])] - P.E[e][q];
-            float t = P.r[a] * dE;
-            if (P.psiB[cb][a] && in_slab(P, a, p[a])) {
-                float* ps = P.psiB[cb][a] + q;
-                const float nv = P.pbB[a][p[a]] * (*ps) + P.pcB[a][p[a]] * dE;
-                *ps = nv;
-                t += nv;
-            }
-            acc += curl_sign(cb, a) * t;
-        }
-        P.B[cb][q] -= acc;
-    }
-}
-
-__global__ void __launch_bounds__(BX* BY* BZ) k_update_E(Params P, Sources S) {
-    int i, j, k;
-    if (!point_of(P, i, j, k)) return;
-    const int p[3] = {i, j, k};
-    const long long q = lin(P, i, j, k);
-    const bool near_src = S.n > 0 && i >= S.bb_lo[0] && i < S.bb_hi[0] && j >= S.bb_lo[1] &&
-                          j < S.bb_hi[1] && k >= S.bb_lo[2] && k < S.bb_hi[2];
-    bool bad = false;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        if (!upd_E(P, c, p)) continue;
-        float eps, st, kt;
-        edge_material(P, c, p, eps, st, kt);
-        const float den = eps + P.theta * st;
-        const float ca = (eps - (1.f - P.theta) * st) / den;
-        const float cb = 1.f / den;
-        float acc = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (a == c) continue;
-            const int h = 3 - c - a;
-            int pp[3] = {i, j, k};
-            pp[a] = prv(P, a, p[a]);
-            const float dH = P.B[h][q] * inv_mu_face(P, h, p) -
-                             P.B[h][lin(P, pp[0], pp[1], pp[2])] * inv_mu_face(P, h, pp);
-            float t = P.r[a] * dH;
-            if (P.psiE[c][a] && in_slab(P, a, p[a])) {
-                float* ps = P.psiE[c][a] + q;
-                const float nv = P.pbE[a][p[a]] * (*ps) + P.pcE[a][p[a]] * dH;
-                *ps = nv;
-                t += nv;
-            }
-            acc += curl_sign(c, a) * t;
-        }
-        const float e = P.E[c][q];
-        float jt = 0.f;
-        if (kt > 0.f) {
-            jt = P.J[c][q] + kt * e;
-            P.J[c][q] = jt;
-        }
-        float en = ca * e + cb * (acc - jt);
-        if (near_src) {
-            for (int s = 0; s < S.n; ++s)
-                if (S.comp[s] == c && i >= S.lo[s][0] && i < S.hi[s][0] && j >= S.lo[s][1] &&
-                    j < S.hi[s][1] && k >= S.lo[s][2] && k < S.hi[s][2])
-                    en += S.amp[s];
-        }
-        P.E[c][q] = en;
-        bad |= !isfinite(en);
-    }
-    if (__any_sync(__activemask(), bad) && bad) atomicOr(P.status, kStatusNonFinite);
-}
-
-__global__ void k_mur(Params P) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int w = blockIdx.z;
-    if (i >= P.N[0] || j >= P.N[1]) return;
-    const int kw = w ? P.n[2] : 0, ki = w ? P.n[2] - 1 : 1;
-    const int p[3] = {i, j, kw};
-    const long long qw = lin(P, i, j, kw), qi = lin(P, i, j, ki);
-    const long long o = (long long)j * P.pitch + i;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        if (!mur_E(P, c, p)) continue;
-        P.E[c][qw] = P.mur_save[(2 * w + c) * P.plane + o] + P.mur_M * (P.E[c][qi] - P.E[c][qw]);
     }
 }
 
@@ -325,22 +211,6 @@ cudaError_t launch_read_field(const Params& P, int comp, int primed, float* dens
 
 cudaError_t launch_probe(const Params& P, const Probes& R, long long n, cudaStream_t st) {
     k_probe<<<R.n, TF_MAX_FREQS, 0, st>>>(P, R, n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_update_B(const Params& P, cudaStream_t st) {
-    k_update_B<<<grid_of(P), dim3(BX, BY, BZ), 0, st>>>(P);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_update_E(const Params& P, const Sources& S, cudaStream_t st) {
-    k_update_E<<<grid_of(P), dim3(BX, BY, BZ), 0, st>>>(P, S);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mur(const Params& P, cudaStream_t st) {
-    dim3 b(32, 8, 1), g((P.N[0] + 31) / 32, (P.N[1] + 7) / 8, 2);
-    k_mur<<<g, b, 0, st>>>(P);
     return cudaGetLastError();
 }
 

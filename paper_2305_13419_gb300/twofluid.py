@@ -269,11 +269,11 @@ class Grid:
 
     def step_timed(self, nsteps: int):
         """Advance like step(); returns {kernel: (mean ms per launch, launches)}."""
-        ms = (C.c_double * 4)()
-        cnt = (C.c_int64 * 4)()
-        _check(load().tf_step_timed(self.h, int(nsteps), ms, cnt, 4), "tf_step_timed")
-        names = ("probe", "update_B", "update_E", "mur")
-        return {names[k]: (ms[k], int(cnt[k])) for k in range(4) if cnt[k]}
+        ms = (C.c_double * 2)()
+        cnt = (C.c_int64 * 2)()
+        _check(load().tf_step_timed(self.h, int(nsteps), ms, cnt, 2), "tf_step_timed")
+        names = ("probe", "step")
+        return {names[k]: (ms[k], int(cnt[k])) for k in range(2) if cnt[k]}
 
     @property
     def level(self) -> int:

@@ -17,8 +17,8 @@ SPEC_TOL = 1e-3    # relative on probe spectra and Q
 
 
 def rel_l2(a, b, floor=0.0):
-    a = np.asarray(a, np.float64)
-    b = np.asarray(b, np.float64)
+    a = np.asarray(a)
+    b = np.asarray(b)
     den = max(float(np.linalg.norm(b)), floor)
     if den == 0.0:
         return float(np.linalg.norm(a))
@@ -31,6 +31,35 @@ def field_floor(c, ref_fields):
     compared absolutely."""
     fam = (c // 3) * 3
     return 1e-6 * max(float(np.linalg.norm(ref_fields[f])) for f in range(fam, fam + 3))
+
+
+FAMILIES = (("E", 0), ("B", 3), ("Js", 6))
+
+
+def family_norms(g):
+    """L2 norm of each vector field (E, B, Js: three components together)."""
+    return {name: float(np.sqrt(sum(np.linalg.norm(g.field(c).astype(np.float64)) ** 2
+                                    for c in range(f, f + 3)))) for name, f in FAMILIES}
+
+
+def compare_families(gg, go, peak=None, tol=FIELD_TOL):
+    """Relative L2 of each vector field, ||gpu - oracle|| / max(||oracle||, peak):
+    `peak` holds the largest norm each field reached during the run, so a
+    transient that has rung down is judged against the scale it had (FP32
+    rounding is relative to the largest values the state carried)."""
+    errs, bad = {}, {}
+    for name, f in FAMILIES:
+        d2 = n2 = 0.0
+        for c in range(f, f + 3):
+            a = gg.field(c).astype(np.float64)
+            b = go.field(c)
+            d2 += float(np.sum((a - b) ** 2))
+            n2 += float(np.sum(b * b))
+        den = max(np.sqrt(n2), (peak or {}).get(name, 0.0))
+        errs[name] = np.sqrt(d2) / den if den > 0 else np.sqrt(d2)
+        if not errs[name] <= tol:
+            bad[name] = errs[name]
+    return errs, bad
 
 
 def set_state(grid, state, float32=True):
