@@ -135,7 +135,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ roofline
-TILE_SX, TILE_SY = 31, 7   # owned columns per tile of the fused step kernel
+TILE_SX, TILE_SY = 32, 8   # owned columns per tile of the fused step kernel
 
 
 def algorithmic_bytes(w, N):
@@ -148,13 +148,16 @@ def algorithmic_bytes(w, N):
        8 B per superconducting edge (Js read + write);
       32 B per CPML slab point and slab axis (two psi_B read old + write new,
                                two psi_E read + write)."""
-    pts = int(N[0]) * int(N[1]) * int(N[2])
+    # points the kernel owns: cells of a walled axis, all points of a periodic
+    # one, planes below the top wall along z
+    own = [N[a] if w.bc[a] == "periodic" else w.n[a] for a in range(3)]
+    pts = own[0] * own[1] * own[2]
     psi = 0
     for a in range(3):
         if w.bc[a] != "cpml":
             continue
         L = w.cpml[a].ncells
-        psi += (2 * L) * (pts // N[a])
+        psi += (2 * L) * (pts // own[a])
     # superconducting edges: an E_c edge is SC if any of its four cells is
     sc = w.lambda_L > 0
     sc_edges = 0
@@ -163,21 +166,21 @@ def algorithmic_bytes(w, N):
         for ax in [2 - b for b in range(3) if b != c]:
             m = m | np.roll(m, 1, axis=ax)
         sc_edges += int(m.sum())
-    # points in non-uniform tile-planes (cells x0-1..x0+30, y0-1..y0+6, k-1..k)
+    # points in non-uniform tile-planes (cells x0-1..x0+31, y0-1..y0+7, k-1..k)
     per = [w.bc[a] == "periodic" for a in range(3)]
     key = np.stack([w.eps_r, w.sigma, w.lambda_L, w.mu_r], axis=-1)
-    kidx = np.arange(N[2])
+    kidx = np.arange(own[2])
     kz = [np.clip(kidx - 1, 0, w.n[2] - 1) if not per[2] else (kidx - 1) % w.n[2],
           np.clip(kidx, 0, w.n[2] - 1)]
     nonuni = 0
     for by in range((N[1] + TILE_SY - 1) // TILE_SY):
-        ys = np.arange(by * TILE_SY - 1, by * TILE_SY + TILE_SY)
+        ys = np.arange(by * TILE_SY - 1, by * TILE_SY + TILE_SY)   # y0-1 .. y0+7
         ys = ys % w.n[1] if per[1] else np.clip(ys, 0, w.n[1] - 1)
-        own_y = min(TILE_SY, N[1] - by * TILE_SY)
-        for bx in range((N[0] + TILE_SX - 1) // TILE_SX):
+        own_y = min(TILE_SY, own[1] - by * TILE_SY)
+        for bx in range((own[0] + TILE_SX - 1) // TILE_SX):
             xs = np.arange(bx * TILE_SX - 1, bx * TILE_SX + TILE_SX)
             xs = xs % w.n[0] if per[0] else np.clip(xs, 0, w.n[0] - 1)
-            own_x = min(TILE_SX, N[0] - bx * TILE_SX)
+            own_x = min(TILE_SX, own[0] - bx * TILE_SX)
             blk = key[:, ys][:, :, xs]                       # [nz][ty][tx][4]
             ref = blk[:, :1, :1]
             same_plane = np.all(blk == ref, axis=(1, 2, 3))  # per cell plane

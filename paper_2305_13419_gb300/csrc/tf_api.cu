@@ -68,8 +68,12 @@ Layout layout_of(const tf_grid_desc* d) {
     L.ncpml_pairs = 0;
     for (int a = 0; a < 3; ++a)
         if (d->bc[a].kind == TF_BC_CPML) L.ncpml_pairs += 2;
-    L.ntx = (L.N[0] + kSX - 1) / kSX;
-    L.nty = (L.N[1] + kSY - 1) / kSY;
+    // tiles cover the cells of a walled axis (its wall plane never changes)
+    // and every point of a periodic one
+    const int cx = d->bc[0].kind == TF_BC_PERIODIC ? L.N[0] : n[0];
+    const int cy = d->bc[1].kind == TF_BC_PERIODIC ? L.N[1] : n[1];
+    L.ntx = (cx + kSX - 1) / kSX;
+    L.nty = (cy + kSY - 1) / kSY;
     L.kend = d->bc[2].kind == TF_BC_PERIODIC ? L.N[2] : L.N[2] - 1;
     L.nch = (L.kend + kChunk - 1) / kChunk;
     const size_t fbytes = align_up(sizeof(float) * (size_t)L.total);
@@ -108,10 +112,12 @@ double waveform(const SrcHost& s, double t) {
 }  // namespace
 
 struct tf_ctx {
+    alignas(128) unsigned char tmap[128];   // TMA descriptor of the 15 field arrays
     tf_grid_desc desc;
     Layout L;
     Params P;
     StepOut O;
+    int parity;         // which of the two E / B buffers holds the current state
     int step_blocks;
     Probes R;
     cudaStream_t stream;
@@ -233,6 +239,14 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
             P.psiE[c][a] = (float*)(base + L.off_psi + (3 * pair + 2) * fbytes);
             ++pair;
         }
+    O.ecur = 0;
+    O.bcur = 3;
+    h->parity = 0;
+    if ((long long)P.plane * L.N[2] >= (1LL << 31)) { delete h; return TF_ENOTSUP; }   // 32-bit indexing
+    if (make_field_tensor_map(base + L.off_fields, L.N, L.pitch, fbytes, 15, h->tmap) != cudaSuccess) {
+        delete h;
+        return TF_ECUDA;
+    }
     O.tilemat = (const float4*)(base + L.off_tiles);
     O.ntx = L.ntx;
     O.nty = L.nty;
@@ -289,7 +303,12 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
             return TF_ECUDA;
         }
         const long long items = (long long)L.ntx * L.nty * L.nch;
-        long long nb = (long long)sms * step_blocks_per_sm();
+        const int per_sm = step_blocks_per_sm();
+        if (per_sm < 1) {
+            delete h;
+            return TF_ECUDA;
+        }
+        long long nb = (long long)sms * per_sm;
         h->step_blocks = (int)(nb < items ? nb : items);
     }
     // zero everything but the profiles, then vacuum materials
@@ -440,7 +459,7 @@ cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[1], st);
     const double t1 = (double)(h->level + 1) * h->dt;
     for (int q = 0; q < h->nsrc; ++q) S.amp[q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
-    if (e == cudaSuccess) e = launch_step(h->P, h->O, S, h->step_blocks, st);
+    if (e == cudaSuccess) e = launch_step(h->tmap, h->P, h->O, S, h->step_blocks, st);
     if (ev) cudaEventRecord(ev[2], st);
     // the new state is in O's buffers: swap
     for (int c = 0; c < 3; ++c) {
@@ -448,6 +467,9 @@ cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
         t = h->P.B[c]; h->P.B[c] = h->O.B[c]; h->O.B[c] = t;
         for (int a = 0; a < 3; ++a) { t = h->P.psiB[c][a]; h->P.psiB[c][a] = h->O.psiB[c][a]; h->O.psiB[c][a] = t; }
     }
+    h->parity ^= 1;
+    h->O.ecur = h->parity ? 9 : 0;
+    h->O.bcur = h->parity ? 12 : 3;
     h->O.base += (unsigned long long)h->L.ntx * h->L.nty * h->L.nch + (unsigned long long)h->step_blocks;
     h->level++;
     return e;

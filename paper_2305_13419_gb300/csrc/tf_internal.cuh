@@ -63,9 +63,12 @@ struct Params {
 
 // Fused step (tf_step.cu): the state ping-pongs between two buffers each
 // step; the kernel reads Params' buffers and writes these.
-constexpr int kTX = 32, kTY = 8;             // threads per tile (x, y)
-constexpr int kSX = kTX - 1, kSY = kTY - 1;  // owned columns per tile (one halo column / row)
+constexpr int kTX = 32, kTY = 8;             // threads per CTA = owned columns (x, y)
+constexpr int kSX = kTX, kSY = kTY;          // tile stride
+constexpr int kBoxX = 40, kBoxY = 10;        // TMA box: x0-4 .. x0+35, y0-1 .. y0+8
+constexpr int kStages = 4;                   // planes in flight per CTA
 constexpr int kChunk = 16;                   // z planes per work item
+constexpr long long kSpinLimit = 1LL << 22;  // bounded mbarrier waits
 
 struct StepOut {
     float* E[3];
@@ -75,6 +78,7 @@ struct StepOut {
                              // tile-plane, ca = NaN where the material varies
     int ntx, nty, nch;       // tiles along x, y; z chunks
     int kend;                // planes iterated: N2 (periodic z) or N2 - 1
+    int ecur, bcur;          // index of the current E / B arrays in the tensor map
     unsigned long long* ctr; // work counter (monotone across launches)
     unsigned long long base; // counter value at the start of this launch
 };
@@ -214,7 +218,12 @@ cudaError_t launch_prime(const Params& P, cudaStream_t st);
 cudaError_t launch_read_field(const Params& P, int comp, int primed, float* dense, double scale,
                               cudaStream_t st);
 cudaError_t launch_probe(const Params& P, const Probes& R, long long n, cudaStream_t st);
-cudaError_t launch_step(const Params& P, const StepOut& O, const Sources& S, int blocks, cudaStream_t st);
+struct TensorMapBox;   // opaque 128-byte CUtensorMap holder (tf_step.cu)
+cudaError_t make_field_tensor_map(void* fields_base, const int N[3], int pitch, size_t field_bytes,
+                                  int nfields, void* out128);
+cudaError_t launch_step(const void* tmap128, const Params& P, const StepOut& O, const Sources& S, int blocks,
+                        cudaStream_t st);
+size_t step_smem_bytes();
 cudaError_t launch_tile_materials(const Params& P, float4* tilemat, int ntx, int nty, cudaStream_t st);
 int step_blocks_per_sm();
 cudaError_t launch_fit_q(const double* re, const double* im, const double* fdt, int nfreq,

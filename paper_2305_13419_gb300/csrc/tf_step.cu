@@ -7,20 +7,33 @@
 //   E^{n+1}    = ca E^n + cb (curl(Bt/mu) - Jt^{n+1/2})     (step 3, CPML psi_E)
 // plus soft sources, first-order Mur z walls and the non-finite watchdog.
 //
-// Layout of the work: a CTA of 32 x 8 threads owns one (x, y) column per
-// thread and streams along z through a chunk of planes.  The E update needs
-// B^{n+1/2} at x-1 and y-1, so the tile carries one halo column and one halo
-// row whose B values it recomputes (the tile advances by 31 x 7 owned
-// columns).  x neighbours move by warp shuffles, y neighbours through shared
-// memory, the z neighbour stays in registers (B at k-1) or is prefetched
-// (E at k+1, k+2).  E, B and psi_B ping-pong between two buffers, so halo
-// reads never race with another CTA's writes; Js and psi_E belong to a single
-// owner and update in place.  Work items (tile, z chunk) are handed out by an
-// atomic counter to a grid sized to fill every SM once.
+// Work layout.  A CTA of 32 x 8 threads owns a 32 x 8 column tile and streams
+// it along z through a chunk of planes.  Each plane's E^n and B^{n-1/2}
+// arrive in shared memory by TMA (cp.async.bulk.tensor) as 40 x 10 boxes
+// covering the tile plus its halo, through a ring of kStages buffers whose
+// mbarriers complete on the transferred byte count; one elected thread keeps
+// the ring kStages - 2 planes ahead of the compute.  Per plane:
+//   B phase  every thread forms B^{n+1/2} at its column (E^n of this plane and
+//            the next one, old B, CPML psi_B); warps 0 and 1 also recompute
+//            the y-1 row / x-1 column of B that the E update needs from the
+//            neighbouring tiles; results go to shared memory, owned values to
+//            the new B buffer;
+//   E phase  every thread forms Js^{n+1/2} and E^{n+1} at its column from the
+//            shared B plane, the previous plane's B kept in registers, and the
+//            edge material.
+// E, B and psi_B ping-pong between two buffers (the other tiles only ever
+// read the old ones); Js and psi_E are owned by one thread and update in
+// place.  Work items (tile, z chunk) come from an atomic counter; the grid
+// fills every SM once.  Periodic x / y seams, which TMA cannot wrap, are
+// patched from global memory after the box lands.
 //
 // Edge material: a tile-plane whose cells are all alike carries one precomputed
-// {ca, cb, cj, 1/mu} record and skips the per-cell maps entirely; elsewhere the
-// edge values are averaged from the maps as the edge rule says.
+// {ca, cb, cj, 1/mu} record; elsewhere the edge values are averaged from the
+// per-cell maps as the edge rule says.  An interior tile-plane (uniform
+// material, no wall, no CPML slab, no source, no Mur plane) takes a path with
+// none of those checks.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 
 #include "tf_internal.cuh"
@@ -29,20 +42,53 @@ namespace tf {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+struct __align__(128) StageBuf {   // both TMA destinations 128-byte aligned
+    alignas(128) float e[3][kBoxY][kBoxX];
+    alignas(128) float b[3][kBoxY][kBoxX];
+};
+constexpr unsigned kBoxBytes = 3u * kBoxY * kBoxX * sizeof(float);   // one field, one box
 
-__device__ __forceinline__ float ld(const float* p, bool ok) { return ok ? __ldg(p) : 0.f; }
-
-// CPML memory of a B-side derivative: psi' = b psi + c d, read from the old
-// buffer, written (by the owner) to the new one; returns the curl term + psi'
-__device__ __forceinline__ float psi_b(float t, const float* src, float* dst, int q, float b, float c,
-                                       float d, bool upd, bool owner) {
-    if (!upd) return t;
-    const float nv = b * __ldg(src + q) + c * d;
-    if (owner) dst[q] = nv;
-    return t + nv;
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// bounded wait for phase `phase` of a barrier; false if it never completed
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase) {
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, int x, int y, int z, int f,
+                                             unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(f), "r"(smem_u32(bar))
+        : "memory");
 }
 
+// CPML memory of a B-side derivative: psi' = b psi + c d from the old buffer,
+// written (by the owner) to the new one; returns the curl term + psi'
+__device__ __forceinline__ float psi_b(float t, const float* src, float* dst, int q, float b, float c, float d,
+                                       bool upd, bool store) {
+    if (!upd) return t;
+    const float nv = b * __ldg(src + q) + c * d;
+    if (store) dst[q] = nv;
+    return t + nv;
+}
 // CPML memory of an E-side derivative, in place (single owner)
 __device__ __forceinline__ float psi_e(float t, float* ps, int q, float b, float c, float d) {
     const float nv = b * ps[q] + c * d;
@@ -53,7 +99,6 @@ __device__ __forceinline__ float psi_e(float t, float* ps, int q, float b, float
 struct Mat {
     float ca, cb, cj;
 };
-
 __device__ __forceinline__ Mat edge_coeffs(const Params& P, int c, int gx, int gy, int k) {
     const int p[3] = {gx, gy, k};
     float eps, st, kt;
@@ -61,25 +106,83 @@ __device__ __forceinline__ Mat edge_coeffs(const Params& P, int c, int gx, int g
     const float den = eps + P.theta * st;
     return {(eps - (1.f - P.theta) * st) / den, 1.f / den, kt};
 }
-
 __device__ __forceinline__ float imu(const Params& P, int c, int gx, int gy, int k) {
     const int p[3] = {gx, gy, k};
     return inv_mu_face(P, c, p);
 }
 
+// wrap (periodic) a coordinate into [0, N); -1 if it falls outside a non-periodic axis
+__device__ __forceinline__ int wrap_or_out(const Params& P, int a, int v) {
+    if (v >= 0 && v < P.N[a]) return v;
+    if (!P.per[a]) return -1;
+    v %= P.N[a];
+    return v < 0 ? v + P.N[a] : v;
+}
+
+// B^{n+1/2} at one point of a landed stage, general path (masks and CPML)
+struct BPoint {
+    float x, y, z;
+};
+__device__ __forceinline__ BPoint b_general(const Params& P, const StepOut& O, const StageBuf& s0,
+                                            const StageBuf& s1, int j, int i, int gx, int gy, int k, int q,
+                                            bool store_psi) {
+    const float ex = s0.e[0][j][i], ey = s0.e[1][j][i], ez = s0.e[2][j][i];
+    const float dEz_y = s0.e[2][j + 1][i] - ez, dEy_z = s1.e[1][j][i] - ey;
+    const float dEx_z = s1.e[0][j][i] - ex, dEz_x = s0.e[2][j][i + 1] - ez;
+    const float dEy_x = s0.e[1][j][i + 1] - ey, dEx_y = s0.e[0][j + 1][i] - ex;
+    float tBx_y = P.r[1] * dEz_y, tBx_z = P.r[2] * dEy_z;
+    float tBy_z = P.r[2] * dEx_z, tBy_x = P.r[0] * dEz_x;
+    float tBz_x = P.r[0] * dEy_x, tBz_y = P.r[1] * dEx_y;
+    const bool hvx = P.per[0] || gx < P.n[0], inx = P.per[0] || (gx >= 1 && gx <= P.n[0] - 1);
+    const bool hvy = P.per[1] || gy < P.n[1], iny = P.per[1] || (gy >= 1 && gy <= P.n[1] - 1);
+    const bool hvz = P.per[2] || k < P.n[2], inz = P.per[2] || (k >= 1 && k <= P.n[2] - 1);
+    const bool uBx = inx && hvy && hvz, uBy = hvx && iny && hvz, uBz = hvx && hvy && inz;
+    if (in_slab(P, 1, gy)) {
+        if (P.psiB[0][1]) tBx_y = psi_b(tBx_y, P.psiB[0][1], O.psiB[0][1], q, P.pbB[1][gy], P.pcB[1][gy], dEz_y, uBx, store_psi);
+        if (P.psiB[2][1]) tBz_y = psi_b(tBz_y, P.psiB[2][1], O.psiB[2][1], q, P.pbB[1][gy], P.pcB[1][gy], dEx_y, uBz, store_psi);
+    }
+    if (in_slab(P, 2, k)) {
+        if (P.psiB[0][2]) tBx_z = psi_b(tBx_z, P.psiB[0][2], O.psiB[0][2], q, P.pbB[2][k], P.pcB[2][k], dEy_z, uBx, store_psi);
+        if (P.psiB[1][2]) tBy_z = psi_b(tBy_z, P.psiB[1][2], O.psiB[1][2], q, P.pbB[2][k], P.pcB[2][k], dEx_z, uBy, store_psi);
+    }
+    if (in_slab(P, 0, gx)) {
+        if (P.psiB[1][0]) tBy_x = psi_b(tBy_x, P.psiB[1][0], O.psiB[1][0], q, P.pbB[0][gx], P.pcB[0][gx], dEz_x, uBy, store_psi);
+        if (P.psiB[2][0]) tBz_x = psi_b(tBz_x, P.psiB[2][0], O.psiB[2][0], q, P.pbB[0][gx], P.pcB[0][gx], dEy_x, uBz, store_psi);
+    }
+    BPoint r;
+    r.x = uBx ? s0.b[0][j][i] - (tBx_y - tBx_z) : s0.b[0][j][i];
+    r.y = uBy ? s0.b[1][j][i] - (tBy_z - tBy_x) : s0.b[1][j][i];
+    r.z = uBz ? s0.b[2][j][i] - (tBz_x - tBz_y) : s0.b[2][j][i];
+    return r;
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(kTX* kTY, 3) k_step(Params P, StepOut O, Sources S) {
-    // double-buffered exchange planes: E^n(k) {x, z} for the y+1 neighbour,
-    // B^{n+1/2}(k) {x, z} for the y-1 neighbour
-    __shared__ float sE[2][2][kTY][kTX], sB[2][2][kTY][kTX];
+__global__ void __launch_bounds__(kTX* kTY, 4)
+    k_step(const __grid_constant__ CUtensorMap tmap, Params P, StepOut O, Sources S) {
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    // TMA destinations must be 128-byte aligned: round the base up (128 spare bytes are allocated)
+    unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+    StageBuf* stg = reinterpret_cast<StageBuf*>(smem_raw);
+    float(*bn)[kBoxY][kBoxX] = reinterpret_cast<float(*)[kBoxY][kBoxX]>(smem_raw + kStages * sizeof(StageBuf));
+    unsigned long long* bar =
+        reinterpret_cast<unsigned long long*>(smem_raw + kStages * sizeof(StageBuf) + 3 * kBoxY * kBoxX * 4);
     __shared__ int s_item;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    __shared__ float4 s_rec[kChunk + 2];   // material record of each plane of the item
+    __shared__ int s_fast[kChunk + 2];     // plane takes the interior path
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
     const int nitems = O.ntx * O.nty * O.nch;
     const int PL = (int)P.plane;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    unsigned long long g = 0;        // planes this CTA has pulled through the ring (stage / phase bookkeeping)
+    unsigned long long issued = 0;   // planes whose copies thread 0 has started
 
     for (;;) {
-        if (tx == 0 && ty == 0) {
+        if (tid == 0) {
             const long long d = (long long)(atomicAdd(O.ctr, 1ull) - O.base);
             s_item = (d >= 0 && d < nitems) ? (int)d : -1;
         }
@@ -87,173 +190,221 @@ __global__ void __launch_bounds__(kTX* kTY, 3) k_step(Params P, StepOut O, Sourc
         const int item = s_item;
         __syncthreads();
         if (item < 0) break;
-        const int ch = item % O.nch;     // consecutive items: consecutive chunks of one tile
+        const int ch = item % O.nch;   // consecutive items: consecutive chunks of one tile
         const int tile = item / O.nch;
         const int bx = tile % O.ntx, by = tile / O.ntx;
+        const int x0 = bx * kSX, y0 = by * kSY;
+        const int kz0 = ch * kChunk, kz1 = min(kz0 + kChunk, O.kend);
+        const bool prev_plane = kz0 > 0 || P.per[2];
+        const int ks = prev_plane ? kz0 - 1 : kz0;
+        const int nq = kz1 - ks + 1;   // planes pulled: ks .. kz1
+        auto plane_of = [&](int qq) {
+            int k = ks + qq;
+            if (k < 0) k += P.N[2];
+            if (k >= P.N[2]) k -= P.N[2];
+            return k;
+        };
+        auto issue = [&](int qq) {   // thread 0 only
+            const unsigned long long gi = g + qq;
+            const int s = (int)(gi % kStages);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar[s], 2 * kBoxBytes);
+            const int k = plane_of(qq);
+            tma_load_box(&stg[s].e[0][0][0], &tmap, x0 - 4, y0 - 1, k, O.ecur, &bar[s]);
+            tma_load_box(&stg[s].b[0][0][0], &tmap, x0 - 4, y0 - 1, k, O.bcur, &bar[s]);
+        };
+        if (tid == 0) {
+            for (int qq = 0; qq < nq && qq < kStages; ++qq) issue(qq);
+            issued = g + (nq < kStages ? nq : kStages);
+        }
 
-        // ---------------------------------------------------------- column
-        const int gx0 = bx * kSX - 1 + tx, gy0 = by * kSY - 1 + ty;
-        int gx = gx0, gy = gy0;
-        bool valid = true;
-        if (gx < 0) { if (P.per[0]) gx += P.N[0]; else valid = false; }
-        if (gy < 0) { if (P.per[1]) gy += P.N[1]; else valid = false; }
-        if (gx >= P.N[0] || gy >= P.N[1]) valid = false;
-        if (!valid) { gx = 0; gy = 0; }
-        const bool owner = valid && tx >= 1 && ty >= 1;
-        const int o = gy * P.pitch + gx;
-        const int gxp = nxt(P, 0, gx), gyp = nxt(P, 1, gy);
-        const int oxp = gy * P.pitch + gxp, oyp = gyp * P.pitch + gx;
-        const bool glob_xp = (tx == kTX - 1) || (gx0 + 1 >= P.N[0]);   // x+1 not in this warp
-        const bool glob_yp = (ty == kTY - 1) || (gy0 + 1 >= P.N[1]);   // y+1 not in this CTA
+        // ------------------------------------------------------- column
+        const int gx = x0 + tx, gy = y0 + ty;
+        const bool valid = gx < P.N[0] && gy < P.N[1];
+        const int o = (valid ? gy : 0) * P.pitch + (valid ? gx : 0);
+        const int i = tx + 4, j = ty + 1;   // position in the box
         const bool hvx = P.per[0] || gx < P.n[0], inx = P.per[0] || (gx >= 1 && gx <= P.n[0] - 1);
         const bool hvy = P.per[1] || gy < P.n[1], iny = P.per[1] || (gy >= 1 && gy <= P.n[1] - 1);
         const bool slx = in_slab(P, 0, gx), sly = in_slab(P, 1, gy);
         const float4* trec = O.tilemat + (long long)(by * O.ntx + bx) * P.N[2];
         const bool mur = P.bc[2] == TF_BC_MUR;
-
-        const int kz0 = ch * kChunk;
-        const int kz1 = min(kz0 + kChunk, O.kend);
-        auto kn = [&](int k) { return (k + 1 < P.N[2]) ? k + 1 : (P.per[2] ? 0 : k); };
-        const bool prev_plane = kz0 > 0 || P.per[2];
-        const int kzm = kz0 > 0 ? kz0 - 1 : P.N[2] - 1;
-
-        // pipeline registers: E^n at k-1, k, k+1; B^{n-1/2}(k); B^{n+1/2} at k-1 and (x, y only) k-2
-        float em[3], e0[3], ep[3], bo[3], bm[3] = {0.f, 0.f, 0.f}, bmm0 = 0.f, bmm1 = 0.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            e0[c] = ld(P.E[c] + kz0 * PL + o, valid);
-            ep[c] = ld(P.E[c] + kn(kz0) * PL + o, valid);
-            em[c] = ld(P.E[c] + kzm * PL + o, valid && prev_plane);
-            bo[c] = ld(P.B[c] + kz0 * PL + o, valid);
+        auto axis_clear = [&](int a, int lo, int hi) {   // columns [lo, hi] interior and outside slabs
+            if (P.per[a]) return true;
+            const int L = P.L[a];
+            return lo >= (L > 0 ? L : 1) && hi < P.n[a] - L && hi <= P.n[a] - 1;
+        };
+        const bool tile_fast = axis_clear(0, x0 - 1, x0 + kSX - 1) && axis_clear(1, y0 - 1, y0 + kSY - 1);
+        auto z_clear = [&](int k) {
+            if (P.per[2]) return true;
+            const int L = P.L[2];
+            return k >= (L > 0 ? L : 1) && k < P.n[2] - L && k <= P.n[2] - 1;
+        };
+        int src_k0 = 1 << 30, src_k1 = -1;   // z range of source planes touching this tile
+        if (S.n > 0 && x0 + kSX > S.bb_lo[0] && x0 <= S.bb_hi[0] && y0 + kSY > S.bb_lo[1] && y0 <= S.bb_hi[1]) {
+            src_k0 = S.bb_lo[2];
+            src_k1 = S.bb_hi[2];
         }
-        // prologue: Bx, By at (x, y, kz0 - 1), the z differences of E(kz0)
-        if (owner && prev_plane) {
-            const int pm = kzm * PL;
-            const bool hvz = P.per[2] || kzm < P.n[2];
-            const bool slz = in_slab(P, 2, kzm);
-            const float ez_yp = __ldg(P.E[2] + pm + oyp), ez_xp = __ldg(P.E[2] + pm + oxp);
-            const bool uBx = inx && hvy && hvz, uBy = hvx && iny && hvz;
-            const float dEz_y = ez_yp - em[2], dEy_z = e0[1] - em[1], dEx_z = e0[0] - em[0], dEz_x = ez_xp - em[2];
-            float tx_y = P.r[1] * dEz_y, tx_z = P.r[2] * dEy_z, ty_z = P.r[2] * dEx_z, ty_x = P.r[0] * dEz_x;
-            const int q = pm + o;
-            if (sly && P.psiB[0][1]) tx_y = psi_b(tx_y, P.psiB[0][1], nullptr, q, P.pbB[1][gy], P.pcB[1][gy], dEz_y, uBx, false);
-            if (slz && P.psiB[0][2]) tx_z = psi_b(tx_z, P.psiB[0][2], nullptr, q, P.pbB[2][kzm], P.pcB[2][kzm], dEy_z, uBx, false);
-            if (slz && P.psiB[1][2]) ty_z = psi_b(ty_z, P.psiB[1][2], nullptr, q, P.pbB[2][kzm], P.pcB[2][kzm], dEx_z, uBy, false);
-            if (slx && P.psiB[1][0]) ty_x = psi_b(ty_x, P.psiB[1][0], nullptr, q, P.pbB[0][gx], P.pcB[0][gx], dEz_x, uBy, false);
-            const float bx_old = __ldg(P.B[0] + q), by_old = __ldg(P.B[1] + q);
-            bm[0] = uBx ? bx_old - (tx_y - tx_z) : bx_old;
-            bm[1] = uBy ? by_old - (ty_z - ty_x) : by_old;
-        }
-        float elo0 = 0.f, elo1 = 0.f;   // E^n on the low Mur wall
-
-        // iteration k: B^{n+1/2}(k) (k < kz1) and E^{n+1}(k-1) (k > kz0)
-        for (int k = kz0; k <= kz1; ++k) {
-            const bool doB = k < kz1, doE = owner && k > kz0;
-            const int b = k & 1;
-            const int ke = k - 1;                       // plane of the E update
-            const int qk = k * PL + o, qe = ke * PL + o;
-            // ---- loads for this iteration and the next
-            float epp[3], bon[3];
-            const int kp2 = kn(kn(k)) * PL + o, kp1 = kn(k) * PL + o;
+        // periodic seams that the TMA box cannot wrap
+        const bool seam = (P.per[0] && (x0 - 4 < 0 || x0 + kBoxX - 4 > P.N[0])) ||
+                          (P.per[1] && (y0 - 1 < 0 || y0 + kBoxY - 1 > P.N[1]));
+        auto patch = [&](StageBuf& sb, int k) {
+            for (int t = tid; t < kBoxY * kBoxX; t += kTX * kTY) {
+                const int jj = t / kBoxX, ii = t % kBoxX;
+                const int x = x0 - 4 + ii, y = y0 - 1 + jj;
+                if (x >= 0 && x < P.N[0] && y >= 0 && y < P.N[1]) continue;
+                const int xw = wrap_or_out(P, 0, x), yw = wrap_or_out(P, 1, y);
+                const bool in = xw >= 0 && yw >= 0;
+                const int qw = k * PL + (in ? yw : 0) * P.pitch + (in ? xw : 0);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                epp[c] = ld(P.E[c] + kp2, valid && doB);
-                bon[c] = ld(P.B[c] + kp1, valid && doB);
-            }
-            float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
-            float jo[3] = {0.f, 0.f, 0.f};
-            bool uni = true;
-            if (doE) {
-                rec = __ldg(trec + ke);
-                uni = !isnan(rec.x);
-                if (!uni || rec.z > 0.f) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) jo[c] = P.J[c][qe];
+                for (int c = 0; c < 3; ++c) {
+                    sb.e[c][jj][ii] = in ? P.E[c][qw] : 0.f;
+                    sb.b[c][jj][ii] = in ? P.B[c][qw] : 0.f;
                 }
             }
-            // ---- exchange E^n(k) with the y+1 row
-            sE[b][0][ty][tx] = e0[0];
-            sE[b][1][ty][tx] = e0[2];
+        };
+
+        // material records and interior flags of the item's planes, read once
+        for (int t = tid; t < nq - 1; t += kTX * kTY) {
+            const int k = plane_of(t);
+            const float4 r = __ldg(trec + k);
+            s_rec[t] = r;
+            s_fast[t] = tile_fast && z_clear(k) && !isnan(r.x) && (k < src_k0 || k >= src_k1) &&
+                        !(mur && (k == 1 || k == P.n[2] - 1));
+        }
+        __syncthreads();
+
+        float bpx = 0.f, bpy = 0.f;     // B^{n+1/2}(k-1) at the own column (z differences)
+        float elo0 = 0.f, elo1 = 0.f;   // E^n on the low Mur wall
+        bool abort = false;
+        for (int qq = 0; qq < nq - 1; ++qq) {
+            const int k = plane_of(qq);
+            const bool doE = ks + qq >= kz0;
+            const unsigned long long g0 = g + qq, g1 = g0 + 1;
+            StageBuf& s0 = stg[g0 % kStages];
+            StageBuf& s1 = stg[g1 % kStages];
+            bool ok = mbar_wait(&bar[g0 % kStages], (unsigned)((g0 / kStages) & 1));
+            ok = ok && mbar_wait(&bar[g1 % kStages], (unsigned)((g1 / kStages) & 1));
+            if (__syncthreads_or(!ok)) {
+                abort = true;
+                break;
+            }
+            if (seam) {
+                if (qq == 0) patch(s0, k);
+                patch(s1, plane_of(qq + 1));
+                __syncthreads();
+            }
+            const int q = k * PL + o;
+            const float4 rec = s_rec[qq];
+            const bool fast = s_fast[qq] != 0;
+            // Js^{n-1/2} of this plane, requested before the B phase so the load overlaps it
+            float jo0 = 0.f, jo1 = 0.f, jo2 = 0.f;
+            if (doE && valid && (isnan(rec.x) || rec.z > 0.f)) {
+                jo0 = P.J[0][q];
+                jo1 = P.J[1][q];
+                jo2 = P.J[2][q];
+            }
+
+            // ------------------------------------------------ B phase
+            if (fast) {
+                const float ex = s0.e[0][j][i], ey = s0.e[1][j][i], ez = s0.e[2][j][i];
+                const float nbx = s0.b[0][j][i] - (P.r[1] * (s0.e[2][j + 1][i] - ez) - P.r[2] * (s1.e[1][j][i] - ey));
+                const float nby = s0.b[1][j][i] - (P.r[2] * (s1.e[0][j][i] - ex) - P.r[0] * (s0.e[2][j][i + 1] - ez));
+                const float nbz = s0.b[2][j][i] - (P.r[0] * (s0.e[1][j][i + 1] - ey) - P.r[1] * (s0.e[0][j + 1][i] - ex));
+                bn[0][j][i] = nbx;
+                bn[1][j][i] = nby;
+                bn[2][j][i] = nbz;
+                if (doE && valid) {
+                    O.B[0][q] = nbx;
+                    O.B[1][q] = nby;
+                    O.B[2][q] = nbz;
+                }
+                if (ty == 0) {   // halo row y0 - 1: Bz, Bx
+                    const int jh = 0;
+                    const float hx = s0.e[0][jh][i], hy = s0.e[1][jh][i], hz = s0.e[2][jh][i];
+                    bn[0][jh][i] = s0.b[0][jh][i] - (P.r[1] * (s0.e[2][jh + 1][i] - hz) - P.r[2] * (s1.e[1][jh][i] - hy));
+                    bn[2][jh][i] = s0.b[2][jh][i] - (P.r[0] * (s0.e[1][jh][i + 1] - hy) - P.r[1] * (s0.e[0][jh + 1][i] - hx));
+                } else if (ty == 1 && tx < kTY) {   // halo column x0 - 1: Bz, By
+                    const int jh = tx + 1, ih = 3;
+                    const float hx = s0.e[0][jh][ih], hy = s0.e[1][jh][ih], hz = s0.e[2][jh][ih];
+                    bn[1][jh][ih] = s0.b[1][jh][ih] - (P.r[2] * (s1.e[0][jh][ih] - hx) - P.r[0] * (s0.e[2][jh][ih + 1] - hz));
+                    bn[2][jh][ih] = s0.b[2][jh][ih] - (P.r[0] * (s0.e[1][jh][ih + 1] - hy) - P.r[1] * (s0.e[0][jh + 1][ih] - hx));
+                }
+            } else {
+                const BPoint bp = b_general(P, O, s0, s1, j, i, valid ? gx : 0, valid ? gy : 0, k, q, doE && valid);
+                bn[0][j][i] = bp.x;
+                bn[1][j][i] = bp.y;
+                bn[2][j][i] = bp.z;
+                if (doE && valid) {
+                    const int p3[3] = {gx, gy, k};
+                    if (upd_B(P, 0, p3)) O.B[0][q] = bp.x;
+                    if (upd_B(P, 1, p3)) O.B[1][q] = bp.y;
+                    if (upd_B(P, 2, p3)) O.B[2][q] = bp.z;
+                }
+                if (ty == 0 || (ty == 1 && tx < kTY)) {
+                    const int jh = ty == 0 ? 0 : tx + 1, ih = ty == 0 ? i : 3;
+                    const int hxg = wrap_or_out(P, 0, x0 - 4 + ih), hyg = wrap_or_out(P, 1, y0 - 1 + jh);
+                    float hxv = 0.f, hyv = 0.f, hzv = 0.f;
+                    if (hxg >= 0 && hyg >= 0) {
+                        const int qh = k * PL + hyg * P.pitch + hxg;
+                        const BPoint h = b_general(P, O, s0, s1, jh, ih, hxg, hyg, k, qh, false);
+                        hxv = h.x;
+                        hyv = h.y;
+                        hzv = h.z;
+                    }
+                    if (ty == 0) {
+                        bn[0][jh][ih] = hxv;
+                        bn[2][jh][ih] = hzv;
+                    } else {
+                        bn[1][jh][ih] = hyv;
+                        bn[2][jh][ih] = hzv;
+                    }
+                }
+            }
             __syncthreads();
 
-            // ------------------------------------------------ B^{n+1/2}(k)
-            float bn[3] = {bo[0], bo[1], bo[2]};
-            {
-                float ey_xp = __shfl_down_sync(kFull, e0[1], 1);
-                float ez_xp = __shfl_down_sync(kFull, e0[2], 1);
-                if (doB) {
-                    const bool hvz = P.per[2] || k < P.n[2];
-                    const bool inz = P.per[2] || (k >= 1 && k <= P.n[2] - 1);
+            // ------------------------------------------------ E phase
+            const float bxo = bn[0][j][i], byo = bn[1][j][i], bzo = bn[2][j][i];
+            if (doE && valid) {
+                const float em0 = s0.e[0][j][i], em1 = s0.e[1][j][i], em2 = s0.e[2][j][i];
+                if (fast) {
+                    const float im = P.uniform_mu ? 1.f : rec.w;
+                    const float cx = im * (P.r[1] * (bzo - bn[2][j - 1][i]) - P.r[2] * (byo - bpy));
+                    const float cy = im * (P.r[2] * (bxo - bpx) - P.r[0] * (bzo - bn[2][j][i - 1]));
+                    const float cz = im * (P.r[0] * (byo - bn[1][j][i - 1]) - P.r[1] * (bxo - bn[0][j - 1][i]));
+                    float j0 = 0.f, j1 = 0.f, j2 = 0.f;
+                    if (rec.z > 0.f) {
+                        j0 = jo0 + rec.z * em0;
+                        j1 = jo1 + rec.z * em1;
+                        j2 = jo2 + rec.z * em2;
+                        P.J[0][q] = j0;
+                        P.J[1][q] = j1;
+                        P.J[2][q] = j2;
+                    }
+                    const float n0 = rec.x * em0 + rec.y * (cx - j0);
+                    const float n1 = rec.x * em1 + rec.y * (cy - j1);
+                    const float n2 = rec.x * em2 + rec.y * (cz - j2);
+                    O.E[0][q] = n0;
+                    O.E[1][q] = n1;
+                    O.E[2][q] = n2;
+                    if (!isfinite(n0 + n1 + n2)) atomicOr(P.status, kStatusNonFinite);
+                } else {
+                    const bool uni = !isnan(rec.x);
+                    const bool hvz = P.per[2] || k < P.n[2], inz = P.per[2] || (k >= 1 && k <= P.n[2] - 1);
                     const bool slz = in_slab(P, 2, k);
-                    if (glob_xp) {
-                        ey_xp = ld(P.E[1] + qk - o + oxp, valid);
-                        ez_xp = ld(P.E[2] + qk - o + oxp, valid);
-                    }
-                    float ex_yp, ez_yp;
-                    if (glob_yp) {
-                        ex_yp = ld(P.E[0] + qk - o + oyp, valid);
-                        ez_yp = ld(P.E[2] + qk - o + oyp, valid);
-                    } else {
-                        ex_yp = sE[b][0][ty + 1][tx];
-                        ez_yp = sE[b][1][ty + 1][tx];
-                    }
-                    const float dEz_y = ez_yp - e0[2], dEy_z = ep[1] - e0[1];
-                    const float dEx_z = ep[0] - e0[0], dEz_x = ez_xp - e0[2];
-                    const float dEy_x = ey_xp - e0[1], dEx_y = ex_yp - e0[0];
-                    float tBx_y = P.r[1] * dEz_y, tBx_z = P.r[2] * dEy_z;
-                    float tBy_z = P.r[2] * dEx_z, tBy_x = P.r[0] * dEz_x;
-                    float tBz_x = P.r[0] * dEy_x, tBz_y = P.r[1] * dEx_y;
-                    const bool uBx = valid && inx && hvy && hvz;
-                    const bool uBy = valid && hvx && iny && hvz;
-                    const bool uBz = valid && hvx && hvy && inz;
-                    if (sly) {
-                        if (P.psiB[0][1]) tBx_y = psi_b(tBx_y, P.psiB[0][1], O.psiB[0][1], qk, P.pbB[1][gy], P.pcB[1][gy], dEz_y, uBx, owner);
-                        if (P.psiB[2][1]) tBz_y = psi_b(tBz_y, P.psiB[2][1], O.psiB[2][1], qk, P.pbB[1][gy], P.pcB[1][gy], dEx_y, uBz, owner);
-                    }
-                    if (slz) {
-                        if (P.psiB[0][2]) tBx_z = psi_b(tBx_z, P.psiB[0][2], O.psiB[0][2], qk, P.pbB[2][k], P.pcB[2][k], dEy_z, uBx, owner);
-                        if (P.psiB[1][2]) tBy_z = psi_b(tBy_z, P.psiB[1][2], O.psiB[1][2], qk, P.pbB[2][k], P.pcB[2][k], dEx_z, uBy, owner);
-                    }
-                    if (slx) {
-                        if (P.psiB[1][0]) tBy_x = psi_b(tBy_x, P.psiB[1][0], O.psiB[1][0], qk, P.pbB[0][gx], P.pcB[0][gx], dEz_x, uBy, owner);
-                        if (P.psiB[2][0]) tBz_x = psi_b(tBz_x, P.psiB[2][0], O.psiB[2][0], qk, P.pbB[0][gx], P.pcB[0][gx], dEy_x, uBz, owner);
-                    }
-                    if (uBx) bn[0] = bo[0] - (tBx_y - tBx_z);
-                    if (uBy) bn[1] = bo[1] - (tBy_z - tBy_x);
-                    if (uBz) bn[2] = bo[2] - (tBz_x - tBz_y);
-                    if (owner) {
-                        if (uBx) O.B[0][qk] = bn[0];
-                        if (uBy) O.B[1][qk] = bn[1];
-                        if (uBz) O.B[2][qk] = bn[2];
-                    }
-                }
-            }
-
-            // ------------------------------------------------ E^{n+1}(k-1)
-            {
-                // B^{n+1/2}(k-1) at x-1 (shuffle) and y-1 (exchange plane of the last iteration)
-                const float bz_xm = __shfl_up_sync(kFull, bm[2], 1);
-                const float by_xm = __shfl_up_sync(kFull, bm[1], 1);
-                if (doE) {
-                    const int bb = b ^ 1;
-                    const float bx_ym = sB[bb][0][ty - 1][tx];
-                    const float bz_ym = sB[bb][1][ty - 1][tx];
-                    const bool hvz = P.per[2] || ke < P.n[2];
-                    const bool inz = P.per[2] || (ke >= 1 && ke <= P.n[2] - 1);
-                    const bool slz = in_slab(P, 2, ke);
                     const bool uEx = hvx && iny && inz, uEy = inx && hvy && inz, uEz = inx && iny && hvz;
-                    float hz = bm[2], hz_ym = bz_ym, hz_xm = bz_xm, hy = bm[1], hy_zm = bmm1, hy_xm = by_xm;
-                    float hx = bm[0], hx_zm = bmm0, hx_ym = bx_ym;
+                    float hz = bzo, hz_ym = bn[2][j - 1][i], hz_xm = bn[2][j][i - 1];
+                    float hy = byo, hy_zm = bpy, hy_xm = bn[1][j][i - 1];
+                    float hx = bxo, hx_zm = bpx, hx_ym = bn[0][j - 1][i];
                     if (!P.uniform_mu) {
                         if (uni) {
                             hz *= rec.w; hz_ym *= rec.w; hz_xm *= rec.w; hy *= rec.w; hy_zm *= rec.w;
                             hy_xm *= rec.w; hx *= rec.w; hx_zm *= rec.w; hx_ym *= rec.w;
                         } else {
-                            const int km = ke > 0 ? ke - 1 : P.N[2] - 1;
+                            const int km = k > 0 ? k - 1 : P.N[2] - 1;
                             const int xm = gx > 0 ? gx - 1 : P.N[0] - 1, ym = gy > 0 ? gy - 1 : P.N[1] - 1;
-                            hz *= imu(P, 2, gx, gy, ke); hz_ym *= imu(P, 2, gx, ym, ke); hz_xm *= imu(P, 2, xm, gy, ke);
-                            hy *= imu(P, 1, gx, gy, ke); hy_zm *= imu(P, 1, gx, gy, km); hy_xm *= imu(P, 1, xm, gy, ke);
-                            hx *= imu(P, 0, gx, gy, ke); hx_zm *= imu(P, 0, gx, gy, km); hx_ym *= imu(P, 0, gx, ym, ke);
+                            hz *= imu(P, 2, gx, gy, k); hz_ym *= imu(P, 2, gx, ym, k); hz_xm *= imu(P, 2, xm, gy, k);
+                            hy *= imu(P, 1, gx, gy, k); hy_zm *= imu(P, 1, gx, gy, km); hy_xm *= imu(P, 1, xm, gy, k);
+                            hx *= imu(P, 0, gx, gy, k); hx_zm *= imu(P, 0, gx, gy, km); hx_ym *= imu(P, 0, gx, ym, k);
                         }
                     }
                     const float dHz_y = hz - hz_ym, dHy_z = hy - hy_zm;
@@ -263,21 +414,22 @@ __global__ void __launch_bounds__(kTX* kTY, 3) k_step(Params P, StepOut O, Sourc
                     float tEy_z = P.r[2] * dHx_z, tEy_x = P.r[0] * dHz_x;
                     float tEz_x = P.r[0] * dHy_x, tEz_y = P.r[1] * dHx_y;
                     if (sly) {
-                        if (uEx && P.psiE[0][1]) tEx_y = psi_e(tEx_y, P.psiE[0][1], qe, P.pbE[1][gy], P.pcE[1][gy], dHz_y);
-                        if (uEz && P.psiE[2][1]) tEz_y = psi_e(tEz_y, P.psiE[2][1], qe, P.pbE[1][gy], P.pcE[1][gy], dHx_y);
+                        if (uEx && P.psiE[0][1]) tEx_y = psi_e(tEx_y, P.psiE[0][1], q, P.pbE[1][gy], P.pcE[1][gy], dHz_y);
+                        if (uEz && P.psiE[2][1]) tEz_y = psi_e(tEz_y, P.psiE[2][1], q, P.pbE[1][gy], P.pcE[1][gy], dHx_y);
                     }
                     if (slz) {
-                        if (uEx && P.psiE[0][2]) tEx_z = psi_e(tEx_z, P.psiE[0][2], qe, P.pbE[2][ke], P.pcE[2][ke], dHy_z);
-                        if (uEy && P.psiE[1][2]) tEy_z = psi_e(tEy_z, P.psiE[1][2], qe, P.pbE[2][ke], P.pcE[2][ke], dHx_z);
+                        if (uEx && P.psiE[0][2]) tEx_z = psi_e(tEx_z, P.psiE[0][2], q, P.pbE[2][k], P.pcE[2][k], dHy_z);
+                        if (uEy && P.psiE[1][2]) tEy_z = psi_e(tEy_z, P.psiE[1][2], q, P.pbE[2][k], P.pcE[2][k], dHx_z);
                     }
                     if (slx) {
-                        if (uEy && P.psiE[1][0]) tEy_x = psi_e(tEy_x, P.psiE[1][0], qe, P.pbE[0][gx], P.pcE[0][gx], dHz_x);
-                        if (uEz && P.psiE[2][0]) tEz_x = psi_e(tEz_x, P.psiE[2][0], qe, P.pbE[0][gx], P.pcE[0][gx], dHy_x);
+                        if (uEy && P.psiE[1][0]) tEy_x = psi_e(tEy_x, P.psiE[1][0], q, P.pbE[0][gx], P.pcE[0][gx], dHz_x);
+                        if (uEz && P.psiE[2][0]) tEz_x = psi_e(tEz_x, P.psiE[2][0], q, P.pbE[0][gx], P.pcE[0][gx], dHy_x);
                     }
                     const float curl[3] = {tEx_y - tEx_z, tEy_z - tEy_x, tEz_x - tEz_y};
                     const bool upd[3] = {uEx, uEy, uEz};
-                    const bool near_src = S.n > 0 && gx >= S.bb_lo[0] && gx < S.bb_hi[0] && gy >= S.bb_lo[1] &&
-                                          gy < S.bb_hi[1] && ke >= S.bb_lo[2] && ke < S.bb_hi[2];
+                    const float em[3] = {em0, em1, em2};
+                    const float jo[3] = {jo0, jo1, jo2};
+                    const bool near_src = k >= src_k0 && k < src_k1;
                     float enew[3];
                     bool bad = false;
 #pragma unroll
@@ -286,55 +438,63 @@ __global__ void __launch_bounds__(kTX* kTY, 3) k_step(Params P, StepOut O, Sourc
                         if (!upd[c]) continue;
                         Mat m;
                         if (uni) m = {rec.x, rec.y, rec.z};
-                        else m = edge_coeffs(P, c, gx, gy, ke);
+                        else m = edge_coeffs(P, c, gx, gy, k);
                         float jt = 0.f;
                         if (m.cj > 0.f) {
                             jt = jo[c] + m.cj * em[c];
-                            P.J[c][qe] = jt;
+                            P.J[c][q] = jt;
                         }
                         float e = m.ca * em[c] + m.cb * (curl[c] - jt);
                         if (near_src) {
                             for (int s = 0; s < S.n; ++s)
                                 if (S.comp[s] == c && gx >= S.lo[s][0] && gx < S.hi[s][0] && gy >= S.lo[s][1] &&
-                                    gy < S.hi[s][1] && ke >= S.lo[s][2] && ke < S.hi[s][2])
+                                    gy < S.hi[s][1] && k >= S.lo[s][2] && k < S.hi[s][2])
                                     e += S.amp[s];
                         }
                         enew[c] = e;
-                        O.E[c][qe] = e;
+                        O.E[c][q] = e;
                         bad |= !isfinite(e);
                     }
                     if (bad) atomicOr(P.status, kStatusNonFinite);
                     // first-order Mur on the z walls: E_w^{n+1} = E_i^n + M (E_i^{n+1} - E_w^n)
                     if (mur) {
                         const bool mx = hvx && iny, my = inx && hvy;
-                        if (ke == 1) {
+                        if (k == 1) {
                             if (mx) O.E[0][o] = em[0] + P.mur_M * (enew[0] - elo0);
                             if (my) O.E[1][o] = em[1] + P.mur_M * (enew[1] - elo1);
                         }
-                        if (ke == P.n[2] - 1) {
+                        if (k == P.n[2] - 1) {
                             const int pw = P.n[2] * PL + o;
-                            if (mx) O.E[0][pw] = em[0] + P.mur_M * (enew[0] - e0[0]);
-                            if (my) O.E[1][pw] = em[1] + P.mur_M * (enew[1] - e0[1]);
+                            if (mx) O.E[0][pw] = em[0] + P.mur_M * (enew[0] - s1.e[0][j][i]);
+                            if (my) O.E[1][pw] = em[1] + P.mur_M * (enew[1] - s1.e[1][j][i]);
                         }
                     }
                 }
             }
-            // publish B^{n+1/2}(k) for the y-1 reads of the next iteration
-            sB[b][0][ty][tx] = bn[0];
-            sB[b][1][ty][tx] = bn[2];
-            if (ke == 0) { elo0 = em[0]; elo1 = em[1]; }
-            bmm0 = bm[0];
-            bmm1 = bm[1];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                bm[c] = bn[c];
-                em[c] = e0[c];
-                e0[c] = ep[c];
-                ep[c] = epp[c];
-                bo[c] = bon[c];
+            if (k == 0) {
+                elo0 = s0.e[0][j][i];
+                elo1 = s0.e[1][j][i];
+            }
+            bpx = bxo;
+            bpy = byo;
+            __syncthreads();   // stage g0 and the B plane are free again
+            if (tid == 0 && qq + kStages < nq) {
+                issue(qq + kStages);
+                ++issued;
             }
         }
-        __syncthreads();   // exchange planes are reused by the next work item
+        if (abort) {
+            // a copy never landed: flag it, give the copies in flight a bounded
+            // time to finish (they write this CTA's shared memory), stop
+            if (tid == 0) {
+                atomicOr(P.status, kStatusTimeout);
+                for (unsigned long long gi = g; gi < issued; ++gi)
+                    mbar_wait(&bar[gi % kStages], (unsigned)((gi / kStages) & 1));
+            }
+            __syncthreads();
+            return;
+        }
+        g += nq;
     }
 }
 
@@ -348,20 +508,26 @@ __global__ void k_tile_materials(Params P, float4* rec, int ntx, int nty) {
         if (v >= P.n[a]) return P.per[a] ? v - P.n[a] : P.n[a] - 1;
         return v;
     };
-    const int cx = cellc(0, bx * kSX - 1 + tx), cy = cellc(1, by * kSY - 1 + ty);
     __shared__ float ref[4];
     for (int k = 0; k < P.N[2]; ++k) {
         const int kz[2] = {cellc(2, k - 1), cellc(2, k)};
         if (tx == 0 && ty == 0) {
-            const long long m = lin(P, cx, cy, kz[1]);
-            ref[0] = P.eps[m]; ref[1] = P.sig[m]; ref[2] = P.kap[m]; ref[3] = P.mu[m];
+            const long long m = lin(P, cellc(0, bx * kSX - 1), cellc(1, by * kSY - 1), kz[1]);
+            ref[0] = P.eps[m];
+            ref[1] = P.sig[m];
+            ref[2] = P.kap[m];
+            ref[3] = P.mu[m];
         }
         __syncthreads();
         bool same = true;
+        // cells x0-1 .. x0+31, y0-1 .. y0+7 (the tile plus its low halo), planes k-1 and k
+        for (int t = ty * kTX + tx; t < (kSX + 1) * (kSY + 1); t += kTX * kTY) {
+            const int cx = cellc(0, bx * kSX - 1 + t % (kSX + 1)), cy = cellc(1, by * kSY - 1 + t / (kSX + 1));
 #pragma unroll
-        for (int z = 0; z < 2; ++z) {
-            const long long m = lin(P, cx, cy, kz[z]);
-            same &= P.eps[m] == ref[0] && P.sig[m] == ref[1] && P.kap[m] == ref[2] && P.mu[m] == ref[3];
+            for (int z = 0; z < 2; ++z) {
+                const long long m = lin(P, cx, cy, kz[z]);
+                same &= P.eps[m] == ref[0] && P.sig[m] == ref[1] && P.kap[m] == ref[2] && P.mu[m] == ref[3];
+            }
         }
         same = __syncthreads_and(same);
         if (tx == 0 && ty == 0) {
@@ -378,14 +544,48 @@ __global__ void k_tile_materials(Params P, float4* rec, int ntx, int nty) {
     }
 }
 
-int step_blocks_per_sm() {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step, kTX * kTY, 0) != cudaSuccess) return 1;
-    return nb > 0 ? nb : 1;
+size_t step_smem_bytes() { return 128 + kStages * sizeof(StageBuf) + 3 * kBoxY * kBoxX * 4 + kStages * 8; }
+
+// opt the kernel in to the dynamic shared memory it needs (above the 48 KB default)
+static cudaError_t step_smem_attribute() {
+    return cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem_bytes());
 }
 
-cudaError_t launch_step(const Params& P, const StepOut& O, const Sources& S, int blocks, cudaStream_t st) {
-    k_step<<<blocks, dim3(kTX, kTY), 0, st>>>(P, O, S);
+int step_blocks_per_sm() {
+    if (step_smem_attribute() != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step, kTX * kTY, step_smem_bytes()) != cudaSuccess)
+        return 1;
+    return nb;
+}
+
+cudaError_t make_field_tensor_map(void* fields_base, const int N[3], int pitch, size_t field_bytes, int nfields,
+                                  void* out128) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    // 4-D view of the field arrays: x (N0 of `pitch` used), y, z, field index
+    const cuuint64_t dims[4] = {(cuuint64_t)N[0], (cuuint64_t)N[1], (cuuint64_t)N[2], (cuuint64_t)nfields};
+    const cuuint64_t strides[3] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * 4 * N[1], (cuuint64_t)field_bytes};
+    const cuuint32_t box[4] = {kBoxX, kBoxY, 1, 3};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode((CUtensorMap*)out128, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, fields_base, dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step(const void* tmap128, const Params& P, const StepOut& O, const Sources& S, int blocks,
+                        cudaStream_t st) {
+    const CUtensorMap* tm = (const CUtensorMap*)tmap128;
+    static cudaError_t attr = step_smem_attribute();
+    if (attr != cudaSuccess) return attr;
+    k_step<<<blocks, dim3(kTX, kTY), step_smem_bytes(), st>>>(*tm, P, O, S);
     return cudaGetLastError();
 }
 
