@@ -194,6 +194,14 @@ tf_status tf_read_field(tf_handle h, int comp, float* dst, int on_device);
 tf_status tf_fit_q(tf_handle h, int id, double f_guess, double q_guess, double* f0,
                    double* alpha, double* q);
 
+/* Watchdog statistics of one stored field array (the non-finite / blow-up
+ * check of the step loop): sum of squares, largest magnitude and number of
+ * NaN / Inf values of component comp over all storage points, in SI units.
+ * E is read at the current integer level, B and Js at the half level the
+ * state holds them (n - 1/2).  Uses a scratch area of the workspace (one
+ * partial per z plane).  Synchronises the stream; any output may be NULL. */
+tf_status tf_field_stats(tf_handle h, int comp, double* sumsq, double* maxabs, int64_t* nonfinite);
+
 const char* tf_strerror(tf_status s);
 
 #ifdef __cplusplus

@@ -24,7 +24,7 @@ struct Layout {
     int ncpml_pairs;        // (component, axis) pairs carrying psi
     int ntx, nty, nch, kend; // fused-step tiles, z chunks, planes iterated
     size_t off_fields, off_maps, off_psi, off_prof, off_zero, off_probe, off_series, off_scratch,
-        off_tiles, off_misc, bytes;
+        off_tiles, off_stats, off_misc, bytes;
     long long scratch_floats;
 };
 
@@ -89,6 +89,7 @@ Layout layout_of(const tf_grid_desc* d) {
     L.scratch_floats = 4 * L.ncell > L.ndense ? 4 * L.ncell : L.ndense;
     L.off_scratch = o; o += align_up(sizeof(float) * (size_t)L.scratch_floats);
     L.off_tiles = o;  o += align_up(sizeof(float4) * (size_t)L.ntx * L.nty * L.N[2]);
+    L.off_stats = o;  o += align_up(sizeof(StatPartial) * (size_t)(L.N[2] + 1));
     L.off_misc = o;   o += kAlign;
     L.bytes = o;
     return L;
@@ -373,6 +374,7 @@ tf_status tf_set_materials(tf_handle h, const float* eps_r, const float* mu_r, c
     TF_CUDA(launch_convert_materials(P, dev[0], dev[1], dev[2], dev[3], h->dt, (float*)P.eps, (float*)P.sig,
                                      (float*)P.kap, (float*)P.mu, h->mm, h->stream));
     TF_CUDA(launch_tile_materials(P, (float4*)h->O.tilemat, h->L.ntx, h->L.nty, h->stream));
+    TF_CUDA(launch_mask_js(P, h->stream));
     unsigned hm[4], st = 0;
     TF_CUDA(cudaMemcpyAsync(hm, h->mm, sizeof(hm), cudaMemcpyDeviceToHost, h->stream));
     TF_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
@@ -586,6 +588,23 @@ tf_status tf_read_field(tf_handle h, int comp, float* dst, int on_device) {
     if (!on_device)
         TF_CUDA(cudaMemcpyAsync(dst, out, sizeof(float) * h->L.ndense, cudaMemcpyDeviceToHost, h->stream));
     TF_CUDA(cudaStreamSynchronize(h->stream));
+    return TF_OK;
+}
+
+tf_status tf_field_stats(tf_handle h, int comp, double* sumsq, double* maxabs, int64_t* nonfinite) {
+    if (!h || comp < 0 || comp > 8) return TF_EINVAL;
+    const float* f = comp < 3 ? h->P.E[comp] : comp < 6 ? h->P.B[comp - 3] : h->P.J[comp - 6];
+    const double scale = comp < 3 ? 1.0 : comp < 6 ? 1.0 / kC0 : kEps0 / h->dt;
+    StatPartial* part = (StatPartial*)(h->ws + h->L.off_stats);
+    StatPartial* out = part + h->L.N[2];
+    TF_CUDA(launch_field_stats(f, h->L.N[0], h->L.N[1], h->L.N[2], h->L.pitch, h->P.plane, scale, part, out,
+                               h->stream));
+    StatPartial r;
+    TF_CUDA(cudaMemcpyAsync(&r, out, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+    TF_CUDA(cudaStreamSynchronize(h->stream));
+    if (sumsq) *sumsq = r.sumsq;
+    if (maxabs) *maxabs = r.maxabs;
+    if (nonfinite) *nonfinite = (int64_t)r.nonfinite;
     return TF_OK;
 }
 

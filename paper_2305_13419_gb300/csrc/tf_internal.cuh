@@ -83,6 +83,13 @@ struct StepOut {
     unsigned long long base; // counter value at the start of this launch
 };
 
+// watchdog statistics of one field array (tf_stats.cu)
+struct StatPartial {
+    double sumsq;                 // sum of squares (SI units)
+    double maxabs;                // largest magnitude
+    unsigned long long nonfinite; // number of NaN / Inf values
+};
+
 struct Sources {
     int n;
     int comp[TF_MAX_SOURCES];
@@ -215,6 +222,7 @@ cudaError_t launch_convert_materials(const Params& P, const float* eps_r, const 
 cudaError_t launch_set_field(const Params& P, int comp, const float* dense, float* dst, double scale,
                              cudaStream_t st);
 cudaError_t launch_prime(const Params& P, cudaStream_t st);
+cudaError_t launch_mask_js(const Params& P, cudaStream_t st);
 cudaError_t launch_read_field(const Params& P, int comp, int primed, float* dense, double scale,
                               cudaStream_t st);
 cudaError_t launch_probe(const Params& P, const Probes& R, long long n, cudaStream_t st);
@@ -226,6 +234,8 @@ cudaError_t launch_step(const void* tmap128, const Params& P, const StepOut& O, 
 size_t step_smem_bytes();
 cudaError_t launch_tile_materials(const Params& P, float4* tilemat, int ntx, int nty, cudaStream_t st);
 int step_blocks_per_sm();
+cudaError_t launch_field_stats(const float* f, int n0, int n1, int n2, int pitch, long long plane, double scale,
+                               StatPartial* partials, StatPartial* out, cudaStream_t st);
 cudaError_t launch_fit_q(const double* re, const double* im, const double* fdt, int nfreq,
                          double dt, long long n0, long long N, double f_guess, double q_guess,
                          double* out, cudaStream_t st);

@@ -102,10 +102,37 @@ __global__ void k_set_field(Params P, int comp, const float* dense, float* dst, 
     const long long r = t / P.N[0];
     const int p[3] = {i, (int)(r % P.N[1]), (int)(r / P.N[1])};
     bool keep;
-    if (comp < 3) keep = upd_E(P, comp, p) || mur_E(P, comp, p);
-    else if (comp < 6) keep = upd_B(P, comp - 3, p);
-    else keep = upd_E(P, comp - 6, p);
+    if (comp < 3) {
+        keep = upd_E(P, comp, p) || mur_E(P, comp, p);
+    } else if (comp < 6) {
+        keep = upd_B(P, comp - 3, p);
+    } else {   // Js lives on superconducting edges only
+        keep = upd_E(P, comp - 6, p);
+        if (keep) {
+            float eps, st, kt;
+            edge_material(P, comp - 6, p, eps, st, kt);
+            keep = kt > 0.f;
+        }
+    }
     dst[lin(P, p[0], p[1], p[2])] = keep ? (float)((double)dense[t] * scale) : 0.f;
+}
+
+// after new materials: Js is zero on every edge that is not superconducting
+__global__ void k_mask_js(Params P) {
+    int i, j, k;
+    if (!point_of(P, i, j, k)) return;
+    const int p[3] = {i, j, k};
+    const long long q = lin(P, i, j, k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        bool keep = upd_E(P, c, p);
+        if (keep) {
+            float eps, st, kt;
+            edge_material(P, c, p, eps, st, kt);
+            keep = kt > 0.f;
+        }
+        if (!keep) P.J[c][q] = 0.f;
+    }
 }
 
 __global__ void k_prime(Params P) {
@@ -194,6 +221,11 @@ cudaError_t launch_set_field(const Params& P, int comp, const float* dense, floa
                              cudaStream_t st) {
     const long long tot = (long long)P.N[0] * P.N[1] * P.N[2];
     k_set_field<<<blocks_for(tot, 256), 256, 0, st>>>(P, comp, dense, dst, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mask_js(const Params& P, cudaStream_t st) {
+    k_mask_js<<<grid_of(P), dim3(BX, BY, BZ), 0, st>>>(P);
     return cudaGetLastError();
 }
 

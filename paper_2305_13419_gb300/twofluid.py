@@ -26,7 +26,7 @@ TF_MAX_PROBES, TF_MAX_FREQS, TF_MAX_SOURCES = 16, 64, 16
 EXPORTS = ["tf_workspace_size", "tf_create", "tf_destroy", "tf_storage_dims", "tf_get_time", "tf_get_dt",
            "tf_set_materials", "tf_set_field", "tf_add_source", "tf_add_probe", "tf_step", "tf_sync",
            "tf_read_probe_dft", "tf_read_probe_series", "tf_read_field", "tf_fit_q", "tf_strerror",
-           "tf_step_timed"]
+           "tf_step_timed", "tf_field_stats"]
 
 
 class TFError(RuntimeError):
@@ -84,7 +84,8 @@ def load(build_if_missing: bool = True):
                        ("tf_read_probe_dft", [vp, C.c_int, dp, dp]),
                        ("tf_read_probe_series", [vp, C.c_int, dp, C.c_int64]),
                        ("tf_read_field", [vp, C.c_int, fp, C.c_int]),
-                       ("tf_fit_q", [vp, C.c_int, C.c_double, C.c_double, dp, dp, dp])):
+                       ("tf_fit_q", [vp, C.c_int, C.c_double, C.c_double, dp, dp, dp]),
+                       ("tf_field_stats", [vp, C.c_int, dp, dp, C.POINTER(C.c_int64)])):
         fn = getattr(L, name)
         fn.restype = st
         fn.argtypes = args
@@ -302,6 +303,12 @@ class Grid:
         p, dev = _ptr(out)
         _check(load().tf_read_field(self.h, int(comp), p, dev), "tf_read_field")
         return out
+
+    def field_stats(self, comp: int):
+        """(sum of squares, max |value|, non-finite count) of one stored field, SI."""
+        s, m, n = C.c_double(), C.c_double(), C.c_int64()
+        _check(load().tf_field_stats(self.h, int(comp), C.byref(s), C.byref(m), C.byref(n)), "tf_field_stats")
+        return s.value, m.value, int(n.value)
 
     def fit_q(self, pid: int, f_guess: float = 0.0, q_guess: float = 100.0):
         f0, al, q = C.c_double(), C.c_double(), C.c_double()

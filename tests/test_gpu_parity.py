@@ -200,3 +200,33 @@ def test_deterministic():
     b = run_gpu(w, 60, st)
     for c in range(9):
         assert np.array_equal(a.field(c), b.field(c))
+
+
+def test_field_stats_watchdog():
+    """Watchdog reduction: sum of squares and max |E| match numpy on the
+    read-back field; injected NaN/Inf values are counted."""
+    from paper_2305_13419_gb300 import twofluid as tf
+    w = W.random_box(n=(20, 13, 17), bc=("cpml", "periodic", "pec"), seed=12, cpml_cells=3)
+    g = tf.Grid.from_workload(w)
+    st = _state(w, 9)
+    for c in range(9):
+        g.set_field(c, st[c].astype(np.float32))
+    for c in (3, 6):        # before the first step B and Js are stored at level 0 (Js on SC edges only)
+        ref = g.field(c).astype(np.float64)
+        s, m, n = g.field_stats(c)
+        assert abs(s / np.sum(ref * ref) - 1) < 1e-6 and abs(m / np.max(np.abs(ref)) - 1) < 1e-6 and n == 0
+    g.step(30)
+    g.sync()
+    for c in range(3):
+        ref = g.field(c).astype(np.float64)
+        s, m, n = g.field_stats(c)
+        assert abs(s / np.sum(ref * ref) - 1) < 1e-9
+        assert m == np.max(np.abs(ref)) and n == 0
+    bad = tf.Grid.from_workload(w)
+    e = np.zeros(bad.shape, np.float32)
+    e[2, 3, 4] = np.nan
+    e[5, 6, 7] = np.inf
+    e[1, 1, 1] = 2.5
+    bad.set_field(0, e)
+    s, m, n = bad.field_stats(0)
+    assert n == 2 and m == 2.5 and abs(s - 6.25) < 1e-12
