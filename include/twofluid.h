@@ -202,6 +202,31 @@ tf_status tf_fit_q(tf_handle h, int id, double f_guess, double q_guess, double* 
  * partial per z plane).  Synchronises the stream; any output may be NULL. */
 tf_status tf_field_stats(tf_handle h, int comp, double* sumsq, double* maxabs, int64_t* nonfinite);
 
+/* Allocation-free twin of tf_field_stats.  The paper has no counterpart: it
+ * exists for callers that cannot allocate device memory when they need the
+ * check -- a monitoring thread that must not take the CUDA allocator's lock
+ * or trigger the device-wide synchronisation of cudaFree while the
+ * simulation runs, or a host application whose memory pool already holds
+ * (nearly) all of the device.  It allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library call.
+ *   field        device pointer to one float32 array of nx_pts x ny_pts x
+ *                nz_pts points, x fastest, rows `pitch` floats apart
+ *                (pitch >= nx_pts), planes pitch * ny_pts floats apart;
+ *   scale        factor applied to every value (1 for values already in SI);
+ *   outputs      sum of squares, largest magnitude, number of NaN / Inf
+ *                values (host pointers; any may be NULL);
+ *   stream       cudaStream_t to run on (NULL = default stream).
+ * Its scratch is a fixed 4097-entry array (about 96 KiB) inside the library
+ * that every GPU loading the library keeps until the process exits; nz_pts
+ * above 4096 is rejected with TF_EINVAL.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device
+ * current, so make that first call before any stream capture.  All calls
+ * share the array and each one overwrites it completely; calls that overlap
+ * on the GPU (different streams or threads at once) race on it.  Synchronises
+ * `stream`. */
+tf_status tf_field_stats_noalloc(const float* field, int nx_pts, int ny_pts, int nz_pts, int pitch, double scale,
+                                 double* sumsq, double* maxabs, int64_t* nonfinite, void* stream);
+
 const char* tf_strerror(tf_status s);
 
 #ifdef __cplusplus

@@ -105,3 +105,69 @@ cudaError_t launch_field_stats(const float* f, int n0, int n1, int n2, int pitch
 
 }  // namespace tf
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant.
+//
+// Some callers cannot allocate device memory at the moment they want the
+// statistics: a monitoring thread that checks a running simulation for
+// blow-ups must not take the CUDA allocator's lock or trigger the device-wide
+// synchronisation that cudaFree implies, and a host application whose memory
+// pool has already reserved (nearly) all of the device cannot get more.  For
+// them the per-plane partials live in a fixed array of this file, sized for
+// kNoAllocMaxPlanes planes, which every GPU that loads the library holds
+// until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int kNoAllocMaxPlanes = 4096;
+constexpr int kMaxDevices = 64;
+
+// partials of one call followed by its result; shared by every call on a device
+static __device__ __align__(256) tf::StatPartial g_stats_scratch[kNoAllocMaxPlanes + 1];
+
+tf::StatPartial* g_scratch_addr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
+
+// device address of g_stats_scratch on the current device (looked up once per device)
+cudaError_t scratch_address(tf::StatPartial** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_stats_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = (tf::StatPartial*)p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" tf_status tf_field_stats_noalloc(const float* field, int nx_pts, int ny_pts, int nz_pts, int pitch,
+                                            double scale, double* sumsq, double* maxabs, int64_t* nonfinite,
+                                            void* stream) {
+    if (!field || nx_pts < 1 || ny_pts < 1 || nz_pts < 1 || pitch < nx_pts) return TF_EINVAL;
+    if ((long long)nx_pts * ny_pts >= (1LL << 31)) return TF_EINVAL;
+    if (nz_pts > kNoAllocMaxPlanes) return TF_EINVAL;   // beyond the fixed scratch
+    tf::StatPartial* scratch = nullptr;
+    if (scratch_address(&scratch) != cudaSuccess) return TF_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long plane = (long long)pitch * ny_pts;
+    if (tf::launch_field_stats(field, nx_pts, ny_pts, nz_pts, pitch, plane, scale, scratch,
+                               scratch + kNoAllocMaxPlanes, st) != cudaSuccess)
+        return TF_ECUDA;
+    tf::StatPartial r;
+    if (cudaMemcpyAsync(&r, scratch + kNoAllocMaxPlanes, sizeof(r), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return TF_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return TF_ECUDA;
+    if (sumsq) *sumsq = r.sumsq;
+    if (maxabs) *maxabs = r.maxabs;
+    if (nonfinite) *nonfinite = (int64_t)r.nonfinite;
+    return TF_OK;
+}

@@ -26,7 +26,7 @@ TF_MAX_PROBES, TF_MAX_FREQS, TF_MAX_SOURCES = 16, 64, 16
 EXPORTS = ["tf_workspace_size", "tf_create", "tf_destroy", "tf_storage_dims", "tf_get_time", "tf_get_dt",
            "tf_set_materials", "tf_set_field", "tf_add_source", "tf_add_probe", "tf_step", "tf_sync",
            "tf_read_probe_dft", "tf_read_probe_series", "tf_read_field", "tf_fit_q", "tf_strerror",
-           "tf_step_timed", "tf_field_stats"]
+           "tf_step_timed", "tf_field_stats", "tf_field_stats_noalloc"]
 
 
 class TFError(RuntimeError):
@@ -85,7 +85,9 @@ def load(build_if_missing: bool = True):
                        ("tf_read_probe_series", [vp, C.c_int, dp, C.c_int64]),
                        ("tf_read_field", [vp, C.c_int, fp, C.c_int]),
                        ("tf_fit_q", [vp, C.c_int, C.c_double, C.c_double, dp, dp, dp]),
-                       ("tf_field_stats", [vp, C.c_int, dp, dp, C.POINTER(C.c_int64)])):
+                       ("tf_field_stats", [vp, C.c_int, dp, dp, C.POINTER(C.c_int64)]),
+                       ("tf_field_stats_noalloc", [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp, dp,
+                                                   C.POINTER(C.c_int64), vp])):
         fn = getattr(L, name)
         fn.restype = st
         fn.argtypes = args
@@ -152,6 +154,17 @@ def tf_step(h, nsteps: int):
 
 def tf_sync(h):
     _check(load().tf_sync(h), "tf_sync")
+
+
+def tf_field_stats_noalloc(field, nx_pts, ny_pts, nz_pts, pitch, scale=1.0, stream=None):
+    """Allocation-free field statistics of a device float32 array (data
+    pointer of a CUDA tensor); returns (sum of squares, max |v|, non-finite)."""
+    s, m, n = C.c_double(), C.c_double(), C.c_int64()
+    ptr = int(field.data_ptr()) if hasattr(field, "data_ptr") else int(field)
+    _check(load().tf_field_stats_noalloc(C.c_void_p(ptr), int(nx_pts), int(ny_pts), int(nz_pts), int(pitch),
+                                         float(scale), C.byref(s), C.byref(m), C.byref(n),
+                                         C.c_void_p(stream)), "tf_field_stats_noalloc")
+    return s.value, m.value, int(n.value)
 
 
 def _ptr(buf):
