@@ -135,7 +135,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ roofline
-TILE_SX, TILE_SY = 32, 8   # owned columns per tile of the fused step kernel
+TILE_SX, TILE_SY = 32, 16   # owned columns per tile of the fused step kernel
 
 
 def algorithmic_bytes(w, N):
@@ -174,7 +174,7 @@ def algorithmic_bytes(w, N):
           np.clip(kidx, 0, w.n[2] - 1)]
     nonuni = 0
     for by in range((N[1] + TILE_SY - 1) // TILE_SY):
-        ys = np.arange(by * TILE_SY - 1, by * TILE_SY + TILE_SY)   # y0-1 .. y0+7
+        ys = np.arange(by * TILE_SY - 1, by * TILE_SY + TILE_SY)   # y0-1 .. y0+15
         ys = ys % w.n[1] if per[1] else np.clip(ys, 0, w.n[1] - 1)
         own_y = min(TILE_SY, own[1] - by * TILE_SY)
         for bx in range((own[0] + TILE_SX - 1) // TILE_SX):

@@ -21,10 +21,10 @@ struct Layout {
     int N[3], pitch;
     long long total;        // floats per field array (padded)
     long long ncell, ndense;
-    int ncpml_pairs;        // (component, axis) pairs carrying psi
+    int ncpml_axes;         // axes with a CPML (6 psi arrays each)
     int ntx, nty, nch, kend; // fused-step tiles, z chunks, planes iterated
     size_t off_fields, off_maps, off_psi, off_prof, off_zero, off_probe, off_series, off_scratch,
-        off_tiles, off_stats, off_misc, bytes;
+        off_tiles, off_stats, off_coef, off_misc, bytes;
     long long scratch_floats;
 };
 
@@ -65,9 +65,9 @@ Layout layout_of(const tf_grid_desc* d) {
     L.total = (long long)L.pitch * L.N[1] * L.N[2];
     L.ncell = (long long)n[0] * n[1] * n[2];
     L.ndense = (long long)L.N[0] * L.N[1] * L.N[2];
-    L.ncpml_pairs = 0;
+    L.ncpml_axes = 0;
     for (int a = 0; a < 3; ++a)
-        if (d->bc[a].kind == TF_BC_CPML) L.ncpml_pairs += 2;
+        if (d->bc[a].kind == TF_BC_CPML) L.ncpml_axes += 1;
     // tiles cover the cells of a walled axis (its wall plane never changes)
     // and every point of a periodic one
     const int cx = d->bc[0].kind == TF_BC_PERIODIC ? L.N[0] : n[0];
@@ -80,7 +80,8 @@ Layout layout_of(const tf_grid_desc* d) {
     size_t o = 0;
     L.off_fields = o; o += 15 * fbytes;   // E, B (two buffers each), Js
     L.off_maps = o;   o += 4 * fbytes;
-    L.off_psi = o;    o += 3 * (size_t)L.ncpml_pairs * fbytes;   // psi_B (two buffers), psi_E
+    L.off_psi = o;    o += 6 * (size_t)L.ncpml_axes * fbytes;   // per axis: psi_B pair x 2 buffers, psi_E pair
+    L.off_coef = o;   o += 9 * fbytes;                             // per-point ca, cb, cj of each E component
     L.off_prof = o;
     for (int a = 0; a < 3; ++a) o += 4 * align_up(sizeof(float) * (size_t)L.N[a]);
     L.off_zero = o;
@@ -113,7 +114,7 @@ double waveform(const SrcHost& s, double t) {
 }  // namespace
 
 struct tf_ctx {
-    alignas(128) unsigned char tmap[128];   // TMA descriptor of the 15 field arrays
+    alignas(128) unsigned char tmap[4][128];   // TMA descriptors: E box, B box, psi_B box, psi_E box
     tf_grid_desc desc;
     Layout L;
     Params P;
@@ -228,23 +229,49 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
     float* maps[4];
     for (int m = 0; m < 4; ++m) maps[m] = (float*)(base + L.off_maps + m * fbytes);
     P.eps = maps[0]; P.sig = maps[1]; P.kap = maps[2]; P.mu = maps[3];
-    int pair = 0;
-    for (int a = 0; a < 3; ++a)
+    // psi arrays: per CPML axis a (slot s), with c1 < c2 the two components != a:
+    //   [psiB(c1) buf0, psiB(c2) buf0, psiB(c1) buf1, psiB(c2) buf1, psiE(c1), psiE(c2)]
+    int slot = 0;
+    for (int a = 0; a < 3; ++a) {
+        O.psi_slot[a] = -1;
         for (int c = 0; c < 3; ++c) {
             P.psiB[c][a] = nullptr;
             P.psiE[c][a] = nullptr;
             O.psiB[c][a] = nullptr;
-            if (desc->bc[a].kind != TF_BC_CPML || c == a) continue;
-            P.psiB[c][a] = (float*)(base + L.off_psi + (3 * pair + 0) * fbytes);
-            O.psiB[c][a] = (float*)(base + L.off_psi + (3 * pair + 1) * fbytes);
-            P.psiE[c][a] = (float*)(base + L.off_psi + (3 * pair + 2) * fbytes);
-            ++pair;
         }
+        if (desc->bc[a].kind != TF_BC_CPML) continue;
+        O.psi_slot[a] = slot;
+        int m = 0;
+        for (int c = 0; c < 3; ++c) {
+            if (c == a) continue;
+            char* g0 = base + L.off_psi + (size_t)(6 * slot) * fbytes;
+            P.psiB[c][a] = (float*)(g0 + (size_t)(0 + m) * fbytes);
+            O.psiB[c][a] = (float*)(g0 + (size_t)(2 + m) * fbytes);
+            P.psiE[c][a] = (float*)(g0 + (size_t)(4 + m) * fbytes);
+            ++m;
+        }
+        ++slot;
+    }
+    O.psib_cur = 0;
+    for (int c = 0; c < 3; ++c) {
+        P.ca[c] = (const float*)(base + L.off_coef + (size_t)(0 + c) * fbytes);
+        P.cb[c] = (const float*)(base + L.off_coef + (size_t)(3 + c) * fbytes);
+        P.cj[c] = (const float*)(base + L.off_coef + (size_t)(6 + c) * fbytes);
+    }
     O.ecur = 0;
     O.bcur = 3;
     h->parity = 0;
     if ((long long)P.plane * L.N[2] >= (1LL << 31)) { delete h; return TF_ENOTSUP; }   // 32-bit indexing
-    if (make_field_tensor_map(base + L.off_fields, L.N, L.pitch, fbytes, 15, h->tmap) != cudaSuccess) {
+    if (make_tensor_map(base + L.off_fields, L.N, L.pitch, fbytes, 15, kEX, kEY, 3, h->tmap[0]) != cudaSuccess ||
+        make_tensor_map(base + L.off_fields, L.N, L.pitch, fbytes, 15, kBX, kBY, 3, h->tmap[1]) != cudaSuccess) {
+        delete h;
+        return TF_ECUDA;
+    }
+    if (L.ncpml_axes > 0 &&
+        (make_tensor_map(base + L.off_psi, L.N, L.pitch, fbytes, 6 * L.ncpml_axes, kBX, kBY, 2, h->tmap[2]) !=
+             cudaSuccess ||
+         make_tensor_map(base + L.off_psi, L.N, L.pitch, fbytes, 6 * L.ncpml_axes, kTX, kTY, 2, h->tmap[3]) !=
+             cudaSuccess)) {
         delete h;
         return TF_ECUDA;
     }
@@ -319,6 +346,7 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
         e = launch_convert_materials(P, nullptr, nullptr, nullptr, nullptr, dt, maps[0], maps[1], maps[2],
                                      maps[3], h->mm, h->stream);
     if (e == cudaSuccess) e = launch_tile_materials(P, (float4*)O.tilemat, L.ntx, L.nty, h->stream);
+    if (e == cudaSuccess) e = launch_edge_coeffs(P, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) { delete h; return TF_ECUDA; }
     *out = h;
@@ -374,6 +402,7 @@ tf_status tf_set_materials(tf_handle h, const float* eps_r, const float* mu_r, c
     TF_CUDA(launch_convert_materials(P, dev[0], dev[1], dev[2], dev[3], h->dt, (float*)P.eps, (float*)P.sig,
                                      (float*)P.kap, (float*)P.mu, h->mm, h->stream));
     TF_CUDA(launch_tile_materials(P, (float4*)h->O.tilemat, h->L.ntx, h->L.nty, h->stream));
+    TF_CUDA(launch_edge_coeffs(P, h->stream));
     TF_CUDA(launch_mask_js(P, h->stream));
     unsigned hm[4], st = 0;
     TF_CUDA(cudaMemcpyAsync(hm, h->mm, sizeof(hm), cudaMemcpyDeviceToHost, h->stream));
@@ -461,7 +490,7 @@ cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
     if (ev) cudaEventRecord(ev[1], st);
     const double t1 = (double)(h->level + 1) * h->dt;
     for (int q = 0; q < h->nsrc; ++q) S.amp[q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
-    if (e == cudaSuccess) e = launch_step(h->tmap, h->P, h->O, S, h->step_blocks, st);
+    if (e == cudaSuccess) e = launch_step(h->tmap[0], h->P, h->O, S, h->step_blocks, st);
     if (ev) cudaEventRecord(ev[2], st);
     // the new state is in O's buffers: swap
     for (int c = 0; c < 3; ++c) {
@@ -470,6 +499,7 @@ cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
         for (int a = 0; a < 3; ++a) { t = h->P.psiB[c][a]; h->P.psiB[c][a] = h->O.psiB[c][a]; h->O.psiB[c][a] = t; }
     }
     h->parity ^= 1;
+    h->O.psib_cur = h->parity ? 2 : 0;
     h->O.ecur = h->parity ? 9 : 0;
     h->O.bcur = h->parity ? 12 : 3;
     h->O.base += (unsigned long long)h->L.ntx * h->L.nty * h->L.nch + (unsigned long long)h->step_blocks;

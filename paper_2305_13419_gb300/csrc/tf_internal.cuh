@@ -52,6 +52,9 @@ struct Params {
     const float* sig;    // sigma dt / eps0 per cell
     const float* kap;    // (c0 dt)^2 / (lambda^2 mu_r) per cell
     const float* mu;     // mu_r per cell
+    const float* ca[3];  // per-point edge coefficients of the theta scheme (used where the
+    const float* cb[3];  //   material of a tile-plane varies): E' = ca E + cb (curl - Jt),
+    const float* cj[3];  //   Jt' = Jt + cj E
     float* psiB[3][3];   // [component][derivative axis], nullptr if absent
     float* psiE[3][3];
     const float* pbE[3]; // CPML b at integer positions along axis a
@@ -63,9 +66,10 @@ struct Params {
 
 // Fused step (tf_step.cu): the state ping-pongs between two buffers each
 // step; the kernel reads Params' buffers and writes these.
-constexpr int kTX = 32, kTY = 8;             // threads per CTA = owned columns (x, y)
+constexpr int kTX = 32, kTY = 16;            // threads per CTA = owned columns (x, y)
 constexpr int kSX = kTX, kSY = kTY;          // tile stride
-constexpr int kBoxX = 40, kBoxY = 10;        // TMA box: x0-4 .. x0+35, y0-1 .. y0+8
+constexpr int kEX = kTX + 8, kEY = kTY + 2;  // E box: x0-4 .. x0+35, y0-1 .. y0+kTY
+constexpr int kBX = kTX + 4, kBY = kTY + 1;  // B / psi_B box: x0-4 .. x0+31, y0-1 .. y0+kTY-1
 constexpr int kStages = 4;                   // planes in flight per CTA
 constexpr int kChunk = 16;                   // z planes per work item
 constexpr long long kSpinLimit = 1LL << 22;  // bounded mbarrier waits
@@ -78,7 +82,9 @@ struct StepOut {
                              // tile-plane, ca = NaN where the material varies
     int ntx, nty, nch;       // tiles along x, y; z chunks
     int kend;                // planes iterated: N2 (periodic z) or N2 - 1
-    int ecur, bcur;          // index of the current E / B arrays in the tensor map
+    int ecur, bcur;          // index of the current E / B arrays in the field tensor map
+    int psi_slot[3];         // per axis: group of 6 psi arrays in the psi tensor map, -1 if no CPML
+    int psib_cur;            // 0 or 2: current psi_B pair inside a group (E pair at 4)
     unsigned long long* ctr; // work counter (monotone across launches)
     unsigned long long base; // counter value at the start of this launch
 };
@@ -226,11 +232,14 @@ cudaError_t launch_mask_js(const Params& P, cudaStream_t st);
 cudaError_t launch_read_field(const Params& P, int comp, int primed, float* dense, double scale,
                               cudaStream_t st);
 cudaError_t launch_probe(const Params& P, const Probes& R, long long n, cudaStream_t st);
-struct TensorMapBox;   // opaque 128-byte CUtensorMap holder (tf_step.cu)
-cudaError_t make_field_tensor_map(void* fields_base, const int N[3], int pitch, size_t field_bytes,
-                                  int nfields, void* out128);
-cudaError_t launch_step(const void* tmap128, const Params& P, const StepOut& O, const Sources& S, int blocks,
+// 4-D TMA view (x, y, z, array index) of `narrays` equally spaced arrays with
+// a box of bx x by x 1 x bf; writes a 128-byte CUtensorMap to out128
+cudaError_t make_tensor_map(void* base, const int N[3], int pitch, size_t array_bytes, int narrays, int bx,
+                            int by, int bf, void* out128);
+// tmaps512: four consecutive 128-byte maps -- E box, B box, psi_B box, psi_E box
+cudaError_t launch_step(const void* tmaps512, const Params& P, const StepOut& O, const Sources& S, int blocks,
                         cudaStream_t st);
+cudaError_t launch_edge_coeffs(const Params& P, cudaStream_t st);
 size_t step_smem_bytes();
 cudaError_t launch_tile_materials(const Params& P, float4* tilemat, int ntx, int nty, cudaStream_t st);
 int step_blocks_per_sm();

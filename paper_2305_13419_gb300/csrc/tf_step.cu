@@ -7,29 +7,29 @@
 //   E^{n+1}    = ca E^n + cb (curl(Bt/mu) - Jt^{n+1/2})     (step 3, CPML psi_E)
 // plus soft sources, first-order Mur z walls and the non-finite watchdog.
 //
-// Work layout.  A CTA of 32 x 8 threads owns a 32 x 8 column tile and streams
-// it along z through a chunk of planes.  Each plane's E^n and B^{n-1/2}
-// arrive in shared memory by TMA (cp.async.bulk.tensor) as 40 x 10 boxes
-// covering the tile plus its halo, through a ring of kStages buffers whose
-// mbarriers complete on the transferred byte count; one elected thread keeps
-// the ring kStages - 2 planes ahead of the compute.  Per plane:
-//   B phase  every thread forms B^{n+1/2} at its column (E^n of this plane and
-//            the next one, old B, CPML psi_B); warps 0 and 1 also recompute
-//            the y-1 row / x-1 column of B that the E update needs from the
-//            neighbouring tiles; results go to shared memory, owned values to
-//            the new B buffer;
+// Work layout.  A CTA of 32 x 16 threads owns a 32 x 16 column tile and
+// streams it along z through a chunk of planes.  Each plane's E^n, B^{n-1/2}
+// and -- in CPML slabs -- the CPML memory of one slab axis arrive in shared
+// memory by TMA (cp.async.bulk.tensor) boxes that cover the tile plus its
+// halo, through a ring of kStages buffers whose mbarriers complete on the
+// transferred byte count.  Thread 0 keeps the ring full, running ahead into
+// the next work item (fetched one item early), so the stream of planes has
+// no gap between items.  Per plane:
+//   B phase  every thread forms B^{n+1/2} at its column; warps 0 and 1 also
+//            recompute the y-1 row / x-1 column of B that the E update needs
+//            from the neighbouring tiles; results go to shared memory, owned
+//            values to the new B buffer;
 //   E phase  every thread forms Js^{n+1/2} and E^{n+1} at its column from the
-//            shared B plane, the previous plane's B kept in registers, and the
-//            edge material.
+//            shared B plane and the previous plane's B kept in registers.
 // E, B and psi_B ping-pong between two buffers (the other tiles only ever
 // read the old ones); Js and psi_E are owned by one thread and update in
 // place.  Work items (tile, z chunk) come from an atomic counter; the grid
 // fills every SM once.  Periodic x / y seams, which TMA cannot wrap, are
 // patched from global memory after the box lands.
 //
-// Edge material: a tile-plane whose cells are all alike carries one precomputed
-// {ca, cb, cj, 1/mu} record; elsewhere the edge values are averaged from the
-// per-cell maps as the edge rule says.  An interior tile-plane (uniform
+// Edge material: a tile-plane whose cells are all alike carries one
+// precomputed {ca, cb, cj, 1/mu} record; elsewhere per-point coefficients
+// (set with the materials) are read.  An interior tile-plane (uniform
 // material, no wall, no CPML slab, no source, no Mur plane) takes a path with
 // none of those checks.
 #include <cuda.h>
@@ -42,11 +42,19 @@ namespace tf {
 
 namespace {
 
-struct __align__(128) StageBuf {   // both TMA destinations 128-byte aligned
-    alignas(128) float e[3][kBoxY][kBoxX];
-    alignas(128) float b[3][kBoxY][kBoxX];
+struct __align__(128) StageBuf {
+    alignas(128) float e[3][kEY][kEX];    // E^n, tile + halo
+    alignas(128) float b[3][kBY][kBX];    // B^{n-1/2}, tile + low halo
+    alignas(128) float pb[2][kBY][kBX];   // psi_B (old) of the slab axis, tile + low halo
+    alignas(128) float pe[2][kTY][kTX];   // psi_E of the slab axis, tile
 };
-constexpr unsigned kBoxBytes = 3u * kBoxY * kBoxX * sizeof(float);   // one field, one box
+constexpr unsigned kEBytes = 3u * kEY * kEX * 4, kBBytes = 3u * kBY * kBX * 4;
+constexpr unsigned kPBBytes = 2u * kBY * kBX * 4, kPEBytes = 2u * kTY * kTX * 4;
+constexpr int kThreads = kTX * kTY;
+
+struct TMaps {
+    CUtensorMap e, b, pb, pe;
+};
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -80,32 +88,9 @@ __device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, 
         : "memory");
 }
 
-// CPML memory of a B-side derivative: psi' = b psi + c d from the old buffer,
-// written (by the owner) to the new one; returns the curl term + psi'
-__device__ __forceinline__ float psi_b(float t, const float* src, float* dst, int q, float b, float c, float d,
-                                       bool upd, bool store) {
-    if (!upd) return t;
-    const float nv = b * __ldg(src + q) + c * d;
-    if (store) dst[q] = nv;
-    return t + nv;
-}
-// CPML memory of an E-side derivative, in place (single owner)
-__device__ __forceinline__ float psi_e(float t, float* ps, int q, float b, float c, float d) {
-    const float nv = b * ps[q] + c * d;
-    ps[q] = nv;
-    return t + nv;
-}
+// position (0 or 1) of component c among the two components != a
+__host__ __device__ __forceinline__ int pair_pos(int c, int a) { return c < 3 - a - c ? 0 : 1; }
 
-struct Mat {
-    float ca, cb, cj;
-};
-__device__ __forceinline__ Mat edge_coeffs(const Params& P, int c, int gx, int gy, int k) {
-    const int p[3] = {gx, gy, k};
-    float eps, st, kt;
-    edge_material(P, c, p, eps, st, kt);
-    const float den = eps + P.theta * st;
-    return {(eps - (1.f - P.theta) * st) / den, 1.f / den, kt};
-}
 __device__ __forceinline__ float imu(const Params& P, int c, int gx, int gy, int k) {
     const int p[3] = {gx, gy, k};
     return inv_mu_face(P, c, p);
@@ -119,13 +104,53 @@ __device__ __forceinline__ int wrap_or_out(const Params& P, int a, int v) {
     return v < 0 ? v + P.N[a] : v;
 }
 
+struct Tile {
+    int x0, y0, kz0, kz1, ks, nq, bx, by;
+};
+__device__ __forceinline__ Tile tile_of(const Params& P, const StepOut& O, int item) {
+    Tile t;
+    const int ch = item % O.nch;   // consecutive items: consecutive chunks of one tile
+    const int tile = item / O.nch;
+    t.bx = tile % O.ntx;
+    t.by = tile / O.ntx;
+    t.x0 = t.bx * kSX;
+    t.y0 = t.by * kSY;
+    t.kz0 = ch * kChunk;
+    t.kz1 = min(t.kz0 + kChunk, O.kend);
+    t.ks = (t.kz0 > 0 || P.per[2]) ? t.kz0 - 1 : t.kz0;
+    t.nq = t.kz1 - t.ks + 1;   // planes pulled: ks .. kz1
+    return t;
+}
+__device__ __forceinline__ int plane_of(const Params& P, const Tile& t, int q) {
+    int k = t.ks + q;
+    if (k < 0) k += P.N[2];
+    if (k >= P.N[2]) k -= P.N[2];
+    return k;
+}
+// the slab axis whose CPML memory travels with the plane (-1: none); z slab
+// planes first, then tiles that touch an x slab, then a y slab
+__device__ __forceinline__ int slab_axis(const Params& P, const Tile& t, int k) {
+    if (P.L[2] > 0 && in_slab(P, 2, k)) return 2;
+    if (P.L[0] > 0 && (t.x0 - 1 < P.L[0] || t.x0 + kSX - 1 >= P.n[0] - P.L[0])) return 0;
+    if (P.L[1] > 0 && (t.y0 - 1 < P.L[1] || t.y0 + kSY - 1 >= P.n[1] - P.L[1])) return 1;
+    return -1;
+}
+
+// old psi_B of (component c, axis a) at a point: from the stage when a is the
+// staged slab axis, else from global memory
+__device__ __forceinline__ float psi_b_old(const Params& P, const StageBuf& s, int sax, int c, int a, int j, int i,
+                                           int q) {
+    if (a == sax) return s.pb[pair_pos(c, a)][j][i];
+    return __ldg(P.psiB[c][a] + q);
+}
+
 // B^{n+1/2} at one point of a landed stage, general path (masks and CPML)
 struct BPoint {
     float x, y, z;
 };
 __device__ __forceinline__ BPoint b_general(const Params& P, const StepOut& O, const StageBuf& s0,
-                                            const StageBuf& s1, int j, int i, int gx, int gy, int k, int q,
-                                            bool store_psi) {
+                                            const StageBuf& s1, int sax, int j, int i, int gx, int gy, int k,
+                                            int q, bool store_psi) {
     const float ex = s0.e[0][j][i], ey = s0.e[1][j][i], ez = s0.e[2][j][i];
     const float dEz_y = s0.e[2][j + 1][i] - ez, dEy_z = s1.e[1][j][i] - ey;
     const float dEx_z = s1.e[0][j][i] - ex, dEz_x = s0.e[2][j][i + 1] - ez;
@@ -137,17 +162,24 @@ __device__ __forceinline__ BPoint b_general(const Params& P, const StepOut& O, c
     const bool hvy = P.per[1] || gy < P.n[1], iny = P.per[1] || (gy >= 1 && gy <= P.n[1] - 1);
     const bool hvz = P.per[2] || k < P.n[2], inz = P.per[2] || (k >= 1 && k <= P.n[2] - 1);
     const bool uBx = inx && hvy && hvz, uBy = hvx && iny && hvz, uBz = hvx && hvy && inz;
-    if (in_slab(P, 1, gy)) {
-        if (P.psiB[0][1]) tBx_y = psi_b(tBx_y, P.psiB[0][1], O.psiB[0][1], q, P.pbB[1][gy], P.pcB[1][gy], dEz_y, uBx, store_psi);
-        if (P.psiB[2][1]) tBz_y = psi_b(tBz_y, P.psiB[2][1], O.psiB[2][1], q, P.pbB[1][gy], P.pcB[1][gy], dEx_y, uBz, store_psi);
+    // psi' = b psi + c d (old buffer), stored by the owner into the new buffer
+    auto psi = [&](float& t, int c, int a, int pa, float d, bool u) {
+        if (!u) return;
+        const float nv = P.pbB[a][pa] * psi_b_old(P, s0, sax, c, a, j, i, q) + P.pcB[a][pa] * d;
+        if (store_psi) O.psiB[c][a][q] = nv;
+        t += nv;
+    };
+    if (P.L[1] > 0 && in_slab(P, 1, gy)) {
+        psi(tBx_y, 0, 1, gy, dEz_y, uBx);
+        psi(tBz_y, 2, 1, gy, dEx_y, uBz);
     }
-    if (in_slab(P, 2, k)) {
-        if (P.psiB[0][2]) tBx_z = psi_b(tBx_z, P.psiB[0][2], O.psiB[0][2], q, P.pbB[2][k], P.pcB[2][k], dEy_z, uBx, store_psi);
-        if (P.psiB[1][2]) tBy_z = psi_b(tBy_z, P.psiB[1][2], O.psiB[1][2], q, P.pbB[2][k], P.pcB[2][k], dEx_z, uBy, store_psi);
+    if (P.L[2] > 0 && in_slab(P, 2, k)) {
+        psi(tBx_z, 0, 2, k, dEy_z, uBx);
+        psi(tBy_z, 1, 2, k, dEx_z, uBy);
     }
-    if (in_slab(P, 0, gx)) {
-        if (P.psiB[1][0]) tBy_x = psi_b(tBy_x, P.psiB[1][0], O.psiB[1][0], q, P.pbB[0][gx], P.pcB[0][gx], dEz_x, uBy, store_psi);
-        if (P.psiB[2][0]) tBz_x = psi_b(tBz_x, P.psiB[2][0], O.psiB[2][0], q, P.pbB[0][gx], P.pcB[0][gx], dEy_x, uBz, store_psi);
+    if (P.L[0] > 0 && in_slab(P, 0, gx)) {
+        psi(tBy_x, 1, 0, gx, dEz_x, uBy);
+        psi(tBz_x, 2, 0, gx, dEy_x, uBz);
     }
     BPoint r;
     r.x = uBx ? s0.b[0][j][i] - (tBx_y - tBx_z) : s0.b[0][j][i];
@@ -158,150 +190,210 @@ __device__ __forceinline__ BPoint b_general(const Params& P, const StepOut& O, c
 
 }  // namespace
 
-__global__ void __launch_bounds__(kTX* kTY, 4)
-    k_step(const __grid_constant__ CUtensorMap tmap, Params P, StepOut O, Sources S) {
+__global__ void __launch_bounds__(kThreads, 2)
+    k_step(const __grid_constant__ TMaps tm, Params P, StepOut O, Sources S) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // TMA destinations must be 128-byte aligned: round the base up (128 spare bytes are allocated)
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
     StageBuf* stg = reinterpret_cast<StageBuf*>(smem_raw);
-    float(*bn)[kBoxY][kBoxX] = reinterpret_cast<float(*)[kBoxY][kBoxX]>(smem_raw + kStages * sizeof(StageBuf));
+    float(*bn)[kBY][kBX] = reinterpret_cast<float(*)[kBY][kBX]>(smem_raw + kStages * sizeof(StageBuf));
     unsigned long long* bar =
-        reinterpret_cast<unsigned long long*>(smem_raw + kStages * sizeof(StageBuf) + 3 * kBoxY * kBoxX * 4);
-    __shared__ int s_item;
-    __shared__ float4 s_rec[kChunk + 2];   // material record of each plane of the item
-    __shared__ int s_fast[kChunk + 2];     // plane takes the interior path
+        reinterpret_cast<unsigned long long*>(smem_raw + kStages * sizeof(StageBuf) + 3 * kBY * kBX * 4);
+    __shared__ int s_item[2];               // current and next work item (-1: none)
+    __shared__ float4 s_rec[2][kChunk + 2]; // material record of each plane of the two items
+    __shared__ int s_fast[2][kChunk + 2];   // plane takes the interior path
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
     const int nitems = O.ntx * O.nty * O.nch;
     const int PL = (int)P.plane;
+    const bool mur = P.bc[2] == TF_BC_MUR;
+
+    auto fetch = [&]() -> int {   // thread 0: next work item or -1
+        const long long d = (long long)(atomicAdd(O.ctr, 1ull) - O.base);
+        return (d >= 0 && d < nitems) ? (int)d : -1;
+    };
+    // interior flags need the tile: computed where the records are stored
+    auto axis_clear = [&](int a, int lo, int hi) {   // columns [lo, hi] interior and outside slabs
+        if (P.per[a]) return true;
+        const int L = P.L[a];
+        return lo >= (L > 0 ? L : 1) && hi < P.n[a] - L && hi <= P.n[a] - 1;
+    };
+    auto z_clear = [&](int k) {
+        if (P.per[2]) return true;
+        const int L = P.L[2];
+        return k >= (L > 0 ? L : 1) && k < P.n[2] - L && k <= P.n[2] - 1;
+    };
+    auto src_range = [&](const Tile& t, int& k0, int& k1) {   // z range of source planes touching the tile
+        k0 = 1 << 30;
+        k1 = -1;
+        if (S.n > 0 && t.x0 + kSX > S.bb_lo[0] && t.x0 <= S.bb_hi[0] && t.y0 + kSY > S.bb_lo[1] &&
+            t.y0 <= S.bb_hi[1]) {
+            k0 = S.bb_lo[2];
+            k1 = S.bb_hi[2];
+        }
+    };
+    // the records of an item: loaded (by threads < nq - 1) ...
+    auto rec_load = [&](int item, float4& r) {
+        if (item < 0) return;
+        const Tile t = tile_of(P, O, item);
+        if (tid < t.nq - 1) r = __ldg(O.tilemat + (long long)(t.by * O.ntx + t.bx) * P.N[2] + plane_of(P, t, tid));
+    };
+    // ... and stored with the interior flag, later
+    auto rec_store = [&](int item, int slot, const float4& r) {
+        if (item < 0) return;
+        const Tile t = tile_of(P, O, item);
+        if (tid < t.nq - 1) {
+            const int k = plane_of(P, t, tid);
+            int sk0, sk1;
+            src_range(t, sk0, sk1);
+            const bool tfast = axis_clear(0, t.x0 - 1, t.x0 + kSX - 1) && axis_clear(1, t.y0 - 1, t.y0 + kSY - 1);
+            s_rec[slot][tid] = r;
+            s_fast[slot][tid] = tfast && z_clear(k) && !isnan(r.x) && (k < sk0 || k >= sk1) &&
+                                !(mur && (k == 1 || k == P.n[2] - 1));
+        }
+    };
+
+    // ---------------------------------------------- producer (thread 0 only)
+    // Items are numbered in the order this CTA takes them; item m lives in
+    // slot m & 1, and the slot is refilled with item m + 2 once item m is done.
+    // The producer may therefore run at most one item ahead of the consumer.
+    unsigned long long issued = 0, consumed = 0;   // planes through the ring
+    int p_ord = 0, p_q = 0;                        // producer: item ordinal, next plane
+    int c_ord = 0;                                 // consumer: item ordinal
+    auto issue = [&](const Tile& t, int q, unsigned long long seq) {
+        const int s = (int)(seq % kStages);
+        const int k = plane_of(P, t, q);
+        const int sax = slab_axis(P, t, k);
+        const unsigned bytes = kEBytes + kBBytes + (sax >= 0 ? kPBBytes + kPEBytes : 0u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&bar[s], bytes);
+        tma_load_box(&stg[s].e[0][0][0], &tm.e, t.x0 - 4, t.y0 - 1, k, O.ecur, &bar[s]);
+        tma_load_box(&stg[s].b[0][0][0], &tm.b, t.x0 - 4, t.y0 - 1, k, O.bcur, &bar[s]);
+        if (sax >= 0) {
+            const int g = 6 * O.psi_slot[sax];
+            tma_load_box(&stg[s].pb[0][0][0], &tm.pb, t.x0 - 4, t.y0 - 1, k, g + O.psib_cur, &bar[s]);
+            tma_load_box(&stg[s].pe[0][0][0], &tm.pe, t.x0, t.y0, k, g + 4, &bar[s]);
+        }
+    };
+    auto pump = [&]() {   // keep kStages planes in flight, crossing into the next item
+        while (issued < consumed + kStages) {
+            int item = s_item[p_ord & 1];
+            if (item < 0) return;
+            Tile t = tile_of(P, O, item);
+            if (p_q >= t.nq) {
+                if (p_ord > c_ord) return;   // the next slot still holds the current item
+                item = s_item[(p_ord + 1) & 1];
+                if (item < 0) return;
+                ++p_ord;
+                p_q = 0;
+                t = tile_of(P, O, item);
+            }
+            issue(t, p_q, issued);
+            ++p_q;
+            ++issued;
+        }
+    };
+
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_item[0] = fetch();
+        s_item[1] = s_item[0] >= 0 ? fetch() : -1;
     }
     __syncthreads();
-    unsigned long long g = 0;        // planes this CTA has pulled through the ring (stage / phase bookkeeping)
-    unsigned long long issued = 0;   // planes whose copies thread 0 has started
+    {
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+        rec_load(s_item[0], r0);
+        rec_load(s_item[1], r1);
+        rec_store(s_item[0], 0, r0);
+        rec_store(s_item[1], 1, r1);
+    }
+    if (tid == 0) pump();
+    __syncthreads();
 
-    for (;;) {
-        if (tid == 0) {
-            const long long d = (long long)(atomicAdd(O.ctr, 1ull) - O.base);
-            s_item = (d >= 0 && d < nitems) ? (int)d : -1;
-        }
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
+    int cur = 0;
+    bool aborted = false;
+    unsigned long long seq0 = 0;   // ring sequence number of plane 0 of the current item
+    while (true) {
+        const int item = s_item[cur];
         if (item < 0) break;
-        const int ch = item % O.nch;   // consecutive items: consecutive chunks of one tile
-        const int tile = item / O.nch;
-        const int bx = tile % O.ntx, by = tile / O.ntx;
-        const int x0 = bx * kSX, y0 = by * kSY;
-        const int kz0 = ch * kChunk, kz1 = min(kz0 + kChunk, O.kend);
-        const bool prev_plane = kz0 > 0 || P.per[2];
-        const int ks = prev_plane ? kz0 - 1 : kz0;
-        const int nq = kz1 - ks + 1;   // planes pulled: ks .. kz1
-        auto plane_of = [&](int qq) {
-            int k = ks + qq;
-            if (k < 0) k += P.N[2];
-            if (k >= P.N[2]) k -= P.N[2];
-            return k;
-        };
-        auto issue = [&](int qq) {   // thread 0 only
-            const unsigned long long gi = g + qq;
-            const int s = (int)(gi % kStages);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&bar[s], 2 * kBoxBytes);
-            const int k = plane_of(qq);
-            tma_load_box(&stg[s].e[0][0][0], &tmap, x0 - 4, y0 - 1, k, O.ecur, &bar[s]);
-            tma_load_box(&stg[s].b[0][0][0], &tmap, x0 - 4, y0 - 1, k, O.bcur, &bar[s]);
-        };
-        if (tid == 0) {
-            for (int qq = 0; qq < nq && qq < kStages; ++qq) issue(qq);
-            issued = g + (nq < kStages ? nq : kStages);
-        }
+        const Tile t = tile_of(P, O, item);
+        const int x0 = t.x0, y0 = t.y0, kz0 = t.kz0, nq = t.nq;
 
         // ------------------------------------------------------- column
         const int gx = x0 + tx, gy = y0 + ty;
         const bool valid = gx < P.N[0] && gy < P.N[1];
         const int o = (valid ? gy : 0) * P.pitch + (valid ? gx : 0);
-        const int i = tx + 4, j = ty + 1;   // position in the box
+        const int i = tx + 4, j = ty + 1;   // position in the E / B boxes
         const bool hvx = P.per[0] || gx < P.n[0], inx = P.per[0] || (gx >= 1 && gx <= P.n[0] - 1);
         const bool hvy = P.per[1] || gy < P.n[1], iny = P.per[1] || (gy >= 1 && gy <= P.n[1] - 1);
-        const bool slx = in_slab(P, 0, gx), sly = in_slab(P, 1, gy);
-        const float4* trec = O.tilemat + (long long)(by * O.ntx + bx) * P.N[2];
-        const bool mur = P.bc[2] == TF_BC_MUR;
-        auto axis_clear = [&](int a, int lo, int hi) {   // columns [lo, hi] interior and outside slabs
-            if (P.per[a]) return true;
-            const int L = P.L[a];
-            return lo >= (L > 0 ? L : 1) && hi < P.n[a] - L && hi <= P.n[a] - 1;
-        };
-        const bool tile_fast = axis_clear(0, x0 - 1, x0 + kSX - 1) && axis_clear(1, y0 - 1, y0 + kSY - 1);
-        auto z_clear = [&](int k) {
-            if (P.per[2]) return true;
-            const int L = P.L[2];
-            return k >= (L > 0 ? L : 1) && k < P.n[2] - L && k <= P.n[2] - 1;
-        };
-        int src_k0 = 1 << 30, src_k1 = -1;   // z range of source planes touching this tile
-        if (S.n > 0 && x0 + kSX > S.bb_lo[0] && x0 <= S.bb_hi[0] && y0 + kSY > S.bb_lo[1] && y0 <= S.bb_hi[1]) {
-            src_k0 = S.bb_lo[2];
-            src_k1 = S.bb_hi[2];
-        }
+        const bool slx = P.L[0] > 0 && in_slab(P, 0, gx), sly = P.L[1] > 0 && in_slab(P, 1, gy);
+        int src_k0, src_k1;
+        src_range(t, src_k0, src_k1);
         // periodic seams that the TMA box cannot wrap
-        const bool seam = (P.per[0] && (x0 - 4 < 0 || x0 + kBoxX - 4 > P.N[0])) ||
-                          (P.per[1] && (y0 - 1 < 0 || y0 + kBoxY - 1 > P.N[1]));
-        auto patch = [&](StageBuf& sb, int k) {
-            for (int t = tid; t < kBoxY * kBoxX; t += kTX * kTY) {
-                const int jj = t / kBoxX, ii = t % kBoxX;
+        const bool seam = (P.per[0] && (x0 - 4 < 0 || x0 + kEX - 4 > P.N[0])) ||
+                          (P.per[1] && (y0 - 1 < 0 || y0 + kEY - 1 > P.N[1]));
+        auto patch = [&](StageBuf& sb, int k, int sax) {
+            for (int u = tid; u < kEY * kEX; u += kThreads) {
+                const int jj = u / kEX, ii = u % kEX;
                 const int x = x0 - 4 + ii, y = y0 - 1 + jj;
                 if (x >= 0 && x < P.N[0] && y >= 0 && y < P.N[1]) continue;
                 const int xw = wrap_or_out(P, 0, x), yw = wrap_or_out(P, 1, y);
                 const bool in = xw >= 0 && yw >= 0;
                 const int qw = k * PL + (in ? yw : 0) * P.pitch + (in ? xw : 0);
+                const bool inb = jj < kBY && ii < kBX;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     sb.e[c][jj][ii] = in ? P.E[c][qw] : 0.f;
-                    sb.b[c][jj][ii] = in ? P.B[c][qw] : 0.f;
+                    if (inb) sb.b[c][jj][ii] = in ? P.B[c][qw] : 0.f;
+                }
+                if (inb && sax >= 0) {
+                    for (int c = 0; c < 3; ++c) {
+                        if (c == sax) continue;
+                        sb.pb[pair_pos(c, sax)][jj][ii] = in ? P.psiB[c][sax][qw] : 0.f;
+                    }
                 }
             }
         };
-
-        // material records and interior flags of the item's planes, read once
-        for (int t = tid; t < nq - 1; t += kTX * kTY) {
-            const int k = plane_of(t);
-            const float4 r = __ldg(trec + k);
-            s_rec[t] = r;
-            s_fast[t] = tile_fast && z_clear(k) && !isnan(r.x) && (k < src_k0 || k >= src_k1) &&
-                        !(mur && (k == 1 || k == P.n[2] - 1));
-        }
-        __syncthreads();
-
         float bpx = 0.f, bpy = 0.f;     // B^{n+1/2}(k-1) at the own column (z differences)
         float elo0 = 0.f, elo1 = 0.f;   // E^n on the low Mur wall
-        bool abort = false;
         for (int qq = 0; qq < nq - 1; ++qq) {
-            const int k = plane_of(qq);
-            const bool doE = ks + qq >= kz0;
-            const unsigned long long g0 = g + qq, g1 = g0 + 1;
+            const int k = plane_of(P, t, qq);
+            const bool doE = t.ks + qq >= kz0;
+            const unsigned long long g0 = seq0 + qq, g1 = g0 + 1;
             StageBuf& s0 = stg[g0 % kStages];
             StageBuf& s1 = stg[g1 % kStages];
-            bool ok = mbar_wait(&bar[g0 % kStages], (unsigned)((g0 / kStages) & 1));
-            ok = ok && mbar_wait(&bar[g1 % kStages], (unsigned)((g1 / kStages) & 1));
-            if (__syncthreads_or(!ok)) {
-                abort = true;
-                break;
-            }
-            if (seam) {
-                if (qq == 0) patch(s0, k);
-                patch(s1, plane_of(qq + 1));
-                __syncthreads();
-            }
+            const int sax = slab_axis(P, t, k);
+            const float4 rec = s_rec[cur][qq];
+            const bool fast = s_fast[cur][qq] != 0;
             const int q = k * PL + o;
-            const float4 rec = s_rec[qq];
-            const bool fast = s_fast[qq] != 0;
-            // Js^{n-1/2} of this plane, requested before the B phase so the load overlaps it
+            // global reads of this plane that do not depend on the stage: issue first
             float jo0 = 0.f, jo1 = 0.f, jo2 = 0.f;
-            if (doE && valid && (isnan(rec.x) || rec.z > 0.f)) {
+            float mc[9];
+            const bool uni = !isnan(rec.x);
+            if (doE && valid && (!uni || rec.z > 0.f)) {
                 jo0 = P.J[0][q];
                 jo1 = P.J[1][q];
                 jo2 = P.J[2][q];
+            }
+            if (doE && valid && !uni) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    mc[c] = __ldg(P.ca[c] + q);
+                    mc[3 + c] = __ldg(P.cb[c] + q);
+                    mc[6 + c] = __ldg(P.cj[c] + q);
+                }
+            }
+            bool ok = mbar_wait(&bar[g0 % kStages], (unsigned)((g0 / kStages) & 1));
+            ok = ok && mbar_wait(&bar[g1 % kStages], (unsigned)((g1 / kStages) & 1));
+            if (__syncthreads_or(!ok)) {
+                aborted = true;
+                break;
+            }
+            if (seam) {
+                if (qq == 0) patch(s0, k, sax);
+                const int k1 = plane_of(P, t, qq + 1);
+                patch(s1, k1, slab_axis(P, t, k1));
+                __syncthreads();
             }
 
             // ------------------------------------------------ B phase
@@ -330,7 +422,8 @@ __global__ void __launch_bounds__(kTX* kTY, 4)
                     bn[2][jh][ih] = s0.b[2][jh][ih] - (P.r[0] * (s0.e[1][jh][ih + 1] - hy) - P.r[1] * (s0.e[0][jh + 1][ih] - hx));
                 }
             } else {
-                const BPoint bp = b_general(P, O, s0, s1, j, i, valid ? gx : 0, valid ? gy : 0, k, q, doE && valid);
+                const BPoint bp =
+                    b_general(P, O, s0, s1, sax, j, i, valid ? gx : 0, valid ? gy : 0, k, q, doE && valid);
                 bn[0][j][i] = bp.x;
                 bn[1][j][i] = bp.y;
                 bn[2][j][i] = bp.z;
@@ -346,7 +439,7 @@ __global__ void __launch_bounds__(kTX* kTY, 4)
                     float hxv = 0.f, hyv = 0.f, hzv = 0.f;
                     if (hxg >= 0 && hyg >= 0) {
                         const int qh = k * PL + hyg * P.pitch + hxg;
-                        const BPoint h = b_general(P, O, s0, s1, jh, ih, hxg, hyg, k, qh, false);
+                        const BPoint h = b_general(P, O, s0, s1, sax, jh, ih, hxg, hyg, k, qh, false);
                         hxv = h.x;
                         hyv = h.y;
                         hzv = h.z;
@@ -388,9 +481,8 @@ __global__ void __launch_bounds__(kTX* kTY, 4)
                     O.E[2][q] = n2;
                     if (!isfinite(n0 + n1 + n2)) atomicOr(P.status, kStatusNonFinite);
                 } else {
-                    const bool uni = !isnan(rec.x);
                     const bool hvz = P.per[2] || k < P.n[2], inz = P.per[2] || (k >= 1 && k <= P.n[2] - 1);
-                    const bool slz = in_slab(P, 2, k);
+                    const bool slz = P.L[2] > 0 && in_slab(P, 2, k);
                     const bool uEx = hvx && iny && inz, uEy = inx && hvy && inz, uEz = inx && iny && hvz;
                     float hz = bzo, hz_ym = bn[2][j - 1][i], hz_xm = bn[2][j][i - 1];
                     float hy = byo, hy_zm = bpy, hy_xm = bn[1][j][i - 1];
@@ -413,17 +505,24 @@ __global__ void __launch_bounds__(kTX* kTY, 4)
                     float tEx_y = P.r[1] * dHz_y, tEx_z = P.r[2] * dHy_z;
                     float tEy_z = P.r[2] * dHx_z, tEy_x = P.r[0] * dHz_x;
                     float tEz_x = P.r[0] * dHy_x, tEz_y = P.r[1] * dHx_y;
+                    // psi' = b psi + c d, in place; the staged copy serves the slab axis
+                    auto psi = [&](float& tt, int c, int a, int pa, float d) {
+                        const float old = (a == sax) ? s0.pe[pair_pos(c, a)][ty][tx] : P.psiE[c][a][q];
+                        const float nv = P.pbE[a][pa] * old + P.pcE[a][pa] * d;
+                        P.psiE[c][a][q] = nv;
+                        tt += nv;
+                    };
                     if (sly) {
-                        if (uEx && P.psiE[0][1]) tEx_y = psi_e(tEx_y, P.psiE[0][1], q, P.pbE[1][gy], P.pcE[1][gy], dHz_y);
-                        if (uEz && P.psiE[2][1]) tEz_y = psi_e(tEz_y, P.psiE[2][1], q, P.pbE[1][gy], P.pcE[1][gy], dHx_y);
+                        if (uEx) psi(tEx_y, 0, 1, gy, dHz_y);
+                        if (uEz) psi(tEz_y, 2, 1, gy, dHx_y);
                     }
                     if (slz) {
-                        if (uEx && P.psiE[0][2]) tEx_z = psi_e(tEx_z, P.psiE[0][2], q, P.pbE[2][k], P.pcE[2][k], dHy_z);
-                        if (uEy && P.psiE[1][2]) tEy_z = psi_e(tEy_z, P.psiE[1][2], q, P.pbE[2][k], P.pcE[2][k], dHx_z);
+                        if (uEx) psi(tEx_z, 0, 2, k, dHy_z);
+                        if (uEy) psi(tEy_z, 1, 2, k, dHx_z);
                     }
                     if (slx) {
-                        if (uEy && P.psiE[1][0]) tEy_x = psi_e(tEy_x, P.psiE[1][0], q, P.pbE[0][gx], P.pcE[0][gx], dHz_x);
-                        if (uEz && P.psiE[2][0]) tEz_x = psi_e(tEz_x, P.psiE[2][0], q, P.pbE[0][gx], P.pcE[0][gx], dHy_x);
+                        if (uEy) psi(tEy_x, 1, 0, gx, dHz_x);
+                        if (uEz) psi(tEz_x, 2, 0, gx, dHy_x);
                     }
                     const float curl[3] = {tEx_y - tEx_z, tEy_z - tEy_x, tEz_x - tEz_y};
                     const bool upd[3] = {uEx, uEy, uEz};
@@ -436,15 +535,14 @@ __global__ void __launch_bounds__(kTX* kTY, 4)
                     for (int c = 0; c < 3; ++c) {
                         enew[c] = em[c];
                         if (!upd[c]) continue;
-                        Mat m;
-                        if (uni) m = {rec.x, rec.y, rec.z};
-                        else m = edge_coeffs(P, c, gx, gy, k);
+                        const float ca = uni ? rec.x : mc[c], cb = uni ? rec.y : mc[3 + c],
+                                    cj = uni ? rec.z : mc[6 + c];
                         float jt = 0.f;
-                        if (m.cj > 0.f) {
-                            jt = jo[c] + m.cj * em[c];
+                        if (cj > 0.f) {
+                            jt = jo[c] + cj * em[c];
                             P.J[c][q] = jt;
                         }
-                        float e = m.ca * em[c] + m.cb * (curl[c] - jt);
+                        float e = ca * em[c] + cb * (curl[c] - jt);
                         if (near_src) {
                             for (int s = 0; s < S.n; ++s)
                                 if (S.comp[s] == c && gx >= S.lo[s][0] && gx < S.hi[s][0] && gy >= S.lo[s][1] &&
@@ -477,24 +575,38 @@ __global__ void __launch_bounds__(kTX* kTY, 4)
             }
             bpx = bxo;
             bpy = byo;
-            __syncthreads();   // stage g0 and the B plane are free again
-            if (tid == 0 && qq + kStages < nq) {
-                issue(qq + kStages);
-                ++issued;
-            }
-        }
-        if (abort) {
-            // a copy never landed: flag it, give the copies in flight a bounded
-            // time to finish (they write this CTA's shared memory), stop
+            __syncthreads();   // stage g0 (and, after the last plane, g1) and the B plane are free again
             if (tid == 0) {
-                atomicOr(P.status, kStatusTimeout);
-                for (unsigned long long gi = g; gi < issued; ++gi)
-                    mbar_wait(&bar[gi % kStages], (unsigned)((gi / kStages) & 1));
+                consumed = g0 + 1 + (qq == nq - 2 ? 1 : 0);
+                pump();
             }
-            __syncthreads();
-            return;
         }
-        g += nq;
+        if (aborted) break;
+        seq0 += nq;
+        // this item is done: its slot takes the item after the next one
+        if (tid == 0) s_item[cur] = s_item[cur ^ 1] >= 0 ? fetch() : -1;
+        __syncthreads();
+        {
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+            rec_load(s_item[cur], r);
+            rec_store(s_item[cur], cur, r);
+        }
+        cur ^= 1;
+        if (tid == 0) {
+            ++c_ord;
+            pump();
+        }
+        __syncthreads();
+    }
+    if (aborted) {
+        // a copy never landed: flag it, give the copies in flight a bounded
+        // time to finish (they write this CTA's shared memory), stop
+        if (tid == 0) {
+            atomicOr(P.status, kStatusTimeout);
+            for (unsigned long long gi = consumed; gi < issued; ++gi)
+                mbar_wait(&bar[gi % kStages], (unsigned)((gi / kStages) & 1));
+        }
+        __syncthreads();
     }
 }
 
@@ -502,7 +614,7 @@ __global__ void __launch_bounds__(kTX* kTY, 4)
 // touches alike?  Then store {ca, cb, cj, 1/mu}; else ca = NaN
 __global__ void k_tile_materials(Params P, float4* rec, int ntx, int nty) {
     const int bx = blockIdx.x, by = blockIdx.y;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
     auto cellc = [&](int a, int v) {
         if (v < 0) return P.per[a] ? v + P.n[a] : 0;
         if (v >= P.n[a]) return P.per[a] ? v - P.n[a] : P.n[a] - 1;
@@ -511,7 +623,7 @@ __global__ void k_tile_materials(Params P, float4* rec, int ntx, int nty) {
     __shared__ float ref[4];
     for (int k = 0; k < P.N[2]; ++k) {
         const int kz[2] = {cellc(2, k - 1), cellc(2, k)};
-        if (tx == 0 && ty == 0) {
+        if (tid == 0) {
             const long long m = lin(P, cellc(0, bx * kSX - 1), cellc(1, by * kSY - 1), kz[1]);
             ref[0] = P.eps[m];
             ref[1] = P.sig[m];
@@ -520,8 +632,8 @@ __global__ void k_tile_materials(Params P, float4* rec, int ntx, int nty) {
         }
         __syncthreads();
         bool same = true;
-        // cells x0-1 .. x0+31, y0-1 .. y0+7 (the tile plus its low halo), planes k-1 and k
-        for (int t = ty * kTX + tx; t < (kSX + 1) * (kSY + 1); t += kTX * kTY) {
+        // cells x0-1 .. x0+kSX-1, y0-1 .. y0+kSY-1 (the tile plus its low halo), planes k-1 and k
+        for (int t = tid; t < (kSX + 1) * (kSY + 1); t += nth) {
             const int cx = cellc(0, bx * kSX - 1 + t % (kSX + 1)), cy = cellc(1, by * kSY - 1 + t / (kSX + 1));
 #pragma unroll
             for (int z = 0; z < 2; ++z) {
@@ -530,7 +642,7 @@ __global__ void k_tile_materials(Params P, float4* rec, int ntx, int nty) {
             }
         }
         same = __syncthreads_and(same);
-        if (tx == 0 && ty == 0) {
+        if (tid == 0) {
             float4 r;
             if (same) {
                 const float den = ref[0] + P.theta * ref[1];
@@ -544,7 +656,7 @@ __global__ void k_tile_materials(Params P, float4* rec, int ntx, int nty) {
     }
 }
 
-size_t step_smem_bytes() { return 128 + kStages * sizeof(StageBuf) + 3 * kBoxY * kBoxX * 4 + kStages * 8; }
+size_t step_smem_bytes() { return 128 + kStages * sizeof(StageBuf) + 3 * kBY * kBX * 4 + kStages * 8; }
 
 // opt the kernel in to the dynamic shared memory it needs (above the 48 KB default)
 static cudaError_t step_smem_attribute() {
@@ -554,13 +666,13 @@ static cudaError_t step_smem_attribute() {
 int step_blocks_per_sm() {
     if (step_smem_attribute() != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step, kTX * kTY, step_smem_bytes()) != cudaSuccess)
-        return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step, kThreads, step_smem_bytes()) != cudaSuccess)
+        return 0;
     return nb;
 }
 
-cudaError_t make_field_tensor_map(void* fields_base, const int N[3], int pitch, size_t field_bytes, int nfields,
-                                  void* out128) {
+cudaError_t make_tensor_map(void* base, const int N[3], int pitch, size_t array_bytes, int narrays, int bx, int by,
+                            int bf, void* out128) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -569,28 +681,56 @@ cudaError_t make_field_tensor_map(void* fields_base, const int N[3], int pitch, 
         if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    // 4-D view of the field arrays: x (N0 of `pitch` used), y, z, field index
-    const cuuint64_t dims[4] = {(cuuint64_t)N[0], (cuuint64_t)N[1], (cuuint64_t)N[2], (cuuint64_t)nfields};
-    const cuuint64_t strides[3] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * 4 * N[1], (cuuint64_t)field_bytes};
-    const cuuint32_t box[4] = {kBoxX, kBoxY, 1, 3};
+    // 4-D view: x (N0 of `pitch` used), y, z, array index
+    const cuuint64_t dims[4] = {(cuuint64_t)N[0], (cuuint64_t)N[1], (cuuint64_t)N[2], (cuuint64_t)narrays};
+    const cuuint64_t strides[3] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * 4 * N[1], (cuuint64_t)array_bytes};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, (cuuint32_t)bf};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = encode((CUtensorMap*)out128, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, fields_base, dims, strides, box,
-                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = encode((CUtensorMap*)out128, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_step(const void* tmap128, const Params& P, const StepOut& O, const Sources& S, int blocks,
+cudaError_t launch_step(const void* tmaps512, const Params& P, const StepOut& O, const Sources& S, int blocks,
                         cudaStream_t st) {
-    const CUtensorMap* tm = (const CUtensorMap*)tmap128;
     static cudaError_t attr = step_smem_attribute();
     if (attr != cudaSuccess) return attr;
+    const TMaps* tm = (const TMaps*)tmaps512;
     k_step<<<blocks, dim3(kTX, kTY), step_smem_bytes(), st>>>(*tm, P, O, S);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tile_materials(const Params& P, float4* rec, int ntx, int nty, cudaStream_t st) {
-    k_tile_materials<<<dim3(ntx, nty), dim3(kTX, kTY), 0, st>>>(P, rec, ntx, nty);
+    k_tile_materials<<<dim3(ntx, nty), dim3(32, 8), 0, st>>>(P, rec, ntx, nty);
+    return cudaGetLastError();
+}
+
+// per-point edge coefficients of the theta scheme (used where a tile-plane's material varies)
+__global__ void k_edge_coeffs(Params P) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= P.N[0] || j >= P.N[1]) return;
+    const int p[3] = {i, j, k};
+    const long long q = lin(P, i, j, k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float ca = 1.f, cb = 0.f, cj = 0.f;
+        if (upd_E(P, c, p)) {
+            float eps, st, kt;
+            edge_material(P, c, p, eps, st, kt);
+            const float den = eps + P.theta * st;
+            ca = (eps - (1.f - P.theta) * st) / den;
+            cb = 1.f / den;
+            cj = kt;
+        }
+        const_cast<float*>(P.ca[c])[q] = ca;
+        const_cast<float*>(P.cb[c])[q] = cb;
+        const_cast<float*>(P.cj[c])[q] = cj;
+    }
+}
+
+cudaError_t launch_edge_coeffs(const Params& P, cudaStream_t st) {
+    k_edge_coeffs<<<dim3((P.N[0] + 31) / 32, (P.N[1] + 7) / 8, P.N[2]), dim3(32, 8), 0, st>>>(P);
     return cudaGetLastError();
 }
 
