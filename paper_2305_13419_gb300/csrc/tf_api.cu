@@ -24,7 +24,7 @@ struct Layout {
     int ncpml_axes;         // axes with a CPML (6 psi arrays each)
     int ntx, nty, nch, kend; // fused-step tiles, z chunks, planes iterated
     size_t off_fields, off_maps, off_psi, off_prof, off_zero, off_probe, off_series, off_scratch,
-        off_tiles, off_stats, off_coef, off_misc, bytes;
+        off_tiles, off_order, off_stats, off_coef, off_misc, bytes;
     long long scratch_floats;
 };
 
@@ -90,6 +90,7 @@ Layout layout_of(const tf_grid_desc* d) {
     L.scratch_floats = 4 * L.ncell > L.ndense ? 4 * L.ncell : L.ndense;
     L.off_scratch = o; o += align_up(sizeof(float) * (size_t)L.scratch_floats);
     L.off_tiles = o;  o += align_up(sizeof(float4) * (size_t)L.ntx * L.nty * L.N[2]);
+    L.off_order = o;  o += align_up(sizeof(int) * (size_t)L.ntx * L.nty * L.nch);
     L.off_stats = o;  o += align_up(sizeof(StatPartial) * (size_t)(L.N[2] + 1));
     L.off_misc = o;   o += kAlign;
     L.bytes = o;
@@ -114,7 +115,7 @@ double waveform(const SrcHost& s, double t) {
 }  // namespace
 
 struct tf_ctx {
-    alignas(128) unsigned char tmap[4][128];   // TMA descriptors: E box, B box, psi_B box, psi_E box
+    alignas(128) unsigned char tmap[3][128];   // TMA descriptors: E box, B box, psi_B box
     tf_grid_desc desc;
     Layout L;
     Params P;
@@ -126,6 +127,7 @@ struct tf_ctx {
     double dt;
     long long level;
     int primed;
+    int order_dirty;   // the work-item order must be rebuilt before the next step
     char* ws;
     float* scratch;
     unsigned* status;
@@ -268,14 +270,14 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
         return TF_ECUDA;
     }
     if (L.ncpml_axes > 0 &&
-        (make_tensor_map(base + L.off_psi, L.N, L.pitch, fbytes, 6 * L.ncpml_axes, kBX, kBY, 2, h->tmap[2]) !=
-             cudaSuccess ||
-         make_tensor_map(base + L.off_psi, L.N, L.pitch, fbytes, 6 * L.ncpml_axes, kTX, kTY, 2, h->tmap[3]) !=
-             cudaSuccess)) {
+        make_tensor_map(base + L.off_psi, L.N, L.pitch, fbytes, 6 * L.ncpml_axes, kBX, kBY, 2, h->tmap[2]) !=
+            cudaSuccess) {
         delete h;
         return TF_ECUDA;
     }
     O.tilemat = (const float4*)(base + L.off_tiles);
+    O.order = (const int*)(base + L.off_order);
+    h->order_dirty = 1;
     O.ntx = L.ntx;
     O.nty = L.nty;
     O.nch = L.nch;
@@ -402,6 +404,7 @@ tf_status tf_set_materials(tf_handle h, const float* eps_r, const float* mu_r, c
     TF_CUDA(launch_convert_materials(P, dev[0], dev[1], dev[2], dev[3], h->dt, (float*)P.eps, (float*)P.sig,
                                      (float*)P.kap, (float*)P.mu, h->mm, h->stream));
     TF_CUDA(launch_tile_materials(P, (float4*)h->O.tilemat, h->L.ntx, h->L.nty, h->stream));
+    h->order_dirty = 1;
     TF_CUDA(launch_edge_coeffs(P, h->stream));
     TF_CUDA(launch_mask_js(P, h->stream));
     unsigned hm[4], st = 0;
@@ -450,6 +453,7 @@ tf_status tf_add_source(tf_handle h, int comp, const int lo[3], const int hi[3],
     s.kind = kind; s.amp = amp; s.f = f; s.t0 = t0; s.tw = tw;
     if (id) *id = h->nsrc;
     h->nsrc++;
+    h->order_dirty = 1;
     return TF_OK;
 }
 
@@ -507,6 +511,14 @@ cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
     return e;
 }
 
+// rebuild the work-item order after the sources or materials changed
+cudaError_t refresh_order(tf_ctx* h, const Sources& S) {
+    if (!h->order_dirty) return cudaSuccess;
+    const cudaError_t e = launch_item_order(h->P, h->O, S, (int*)h->O.order, h->stream);
+    if (e == cudaSuccess) h->order_dirty = 0;
+    return e;
+}
+
 void fill_sources(const tf_ctx* h, Sources& S) {
     S.n = h->nsrc;
     for (int a = 0; a < 3; ++a) { S.bb_lo[a] = 1 << 30; S.bb_hi[a] = -1; }
@@ -533,6 +545,7 @@ tf_status tf_step(tf_handle h, int64_t nsteps) {
     }
     Sources S;
     fill_sources(h, S);
+    TF_CUDA(refresh_order(h, S));
     for (int64_t s = 0; s < nsteps; ++s) TF_CUDA(launch_one_step(h, S, nullptr));
     return TF_OK;
 }
@@ -558,6 +571,7 @@ tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t*
     const int has[2] = {h->R.n > 0, 1};
     Sources S;
     fill_sources(h, S);
+    if (refresh_order(h, S) != cudaSuccess) rc = TF_ECUDA;
     int64_t done = 0;
     while (rc == TF_OK && done < nsteps) {
         const int m = (int)((nsteps - done) < kRing ? (nsteps - done) : kRing);

@@ -66,7 +66,8 @@ struct Params {
 
 // Fused step (tf_step.cu): the state ping-pongs between two buffers each
 // step; the kernel reads Params' buffers and writes these.
-constexpr int kTX = 32, kTY = 16;            // threads per CTA = owned columns (x, y)
+constexpr int kTX = 32, kTY = 16;            // owned columns per tile (x, y)
+constexpr int kRows = 2;                     // adjacent y rows per thread: kTX x kTY / kRows threads
 constexpr int kSX = kTX, kSY = kTY;          // tile stride
 constexpr int kEX = kTX + 8, kEY = kTY + 2;  // E box: x0-4 .. x0+35, y0-1 .. y0+kTY
 constexpr int kBX = kTX + 4, kBY = kTY + 1;  // B / psi_B box: x0-4 .. x0+31, y0-1 .. y0+kTY-1
@@ -85,6 +86,7 @@ struct StepOut {
     int ecur, bcur;          // index of the current E / B arrays in the field tensor map
     int psi_slot[3];         // per axis: group of 6 psi arrays in the psi tensor map, -1 if no CPML
     int psib_cur;            // 0 or 2: current psi_B pair inside a group (E pair at 4)
+    const int* order;        // work items of a launch in the order they are handed out
     unsigned long long* ctr; // work counter (monotone across launches)
     unsigned long long base; // counter value at the start of this launch
 };
@@ -236,12 +238,14 @@ cudaError_t launch_probe(const Params& P, const Probes& R, long long n, cudaStre
 // a box of bx x by x 1 x bf; writes a 128-byte CUtensorMap to out128
 cudaError_t make_tensor_map(void* base, const int N[3], int pitch, size_t array_bytes, int narrays, int bx,
                             int by, int bf, void* out128);
-// tmaps512: four consecutive 128-byte maps -- E box, B box, psi_B box, psi_E box
-cudaError_t launch_step(const void* tmaps512, const Params& P, const StepOut& O, const Sources& S, int blocks,
+// tmaps: three consecutive 128-byte maps -- E box, B box, psi_B box
+cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, const Sources& S, int blocks,
                         cudaStream_t st);
 cudaError_t launch_edge_coeffs(const Params& P, cudaStream_t st);
 size_t step_smem_bytes();
 cudaError_t launch_tile_materials(const Params& P, float4* tilemat, int ntx, int nty, cudaStream_t st);
+// order in which k_step hands out its work items (items needing the full plane loop first)
+cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int* order, cudaStream_t st);
 int step_blocks_per_sm();
 cudaError_t launch_field_stats(const float* f, int n0, int n1, int n2, int pitch, long long plane, double scale,
                                StatPartial* partials, StatPartial* out, cudaStream_t st);
