@@ -166,39 +166,123 @@ struct V3 {
     float x, y, z;
 };
 
-// B^{n+1/2} before masking at box position (j, i) of landed stages s0 (plane
-// k) and s1 (plane k + 1): the curl update plus the CPML memory of the staged
-// axis sax (coefficients bB, cB; zero outside the slab), whose new values
-// come back in p0, p1 (pair order)
-__device__ __forceinline__ V3 b_update(const Params& P, const StageBuf& s0, const StageBuf& s1, int j, int i,
-                                       int sax, float bB, float cB, float& p0, float& p1) {
-    const float ex = s0.e[0][j][i], ey = s0.e[1][j][i], ez = s0.e[2][j][i];
-    const float dEz_y = s0.e[2][j + 1][i] - ez, dEy_z = s1.e[1][j][i] - ey;
-    const float dEx_z = s1.e[0][j][i] - ex, dEz_x = s0.e[2][j][i + 1] - ez;
-    const float dEy_x = s0.e[1][j][i + 1] - ey, dEx_y = s0.e[0][j + 1][i] - ex;
-    V3 r;
-    r.x = s0.b[0][j][i] - (P.r[1] * dEz_y - P.r[2] * dEy_z);
-    r.y = s0.b[1][j][i] - (P.r[2] * dEx_z - P.r[0] * dEz_x);
-    r.z = s0.b[2][j][i] - (P.r[0] * dEy_x - P.r[1] * dEx_y);
-    p0 = 0.f;
-    p1 = 0.f;
-    if (sax == 0) {          // By, Bz
-        p0 = bB * s0.pb[0][j][i] + cB * dEz_x;
-        p1 = bB * s0.pb[1][j][i] + cB * dEy_x;
-        r.y += p0;
-        r.z -= p1;
-    } else if (sax == 1) {   // Bx, Bz
-        p0 = bB * s0.pb[0][j][i] + cB * dEz_y;
-        p1 = bB * s0.pb[1][j][i] + cB * dEx_y;
-        r.x -= p0;
-        r.z += p1;
-    } else if (sax == 2) {   // Bx, By
-        p0 = bB * s0.pb[0][j][i] + cB * dEy_z;
-        p1 = bB * s0.pb[1][j][i] + cB * dEx_z;
-        r.x += p0;
-        r.y -= p1;
-    }
+// Two horizontally adjacent points travel together: a 64-bit register holds
+// the pair (low: x, high: x + 1) and the sm_100-family packed FP32 pipe
+// (add / sub / mul / fma .f32x2) updates both at once.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(__float_as_uint(a)), "r"(__float_as_uint(b)));
     return r;
+}
+__device__ __forceinline__ float lo(f2 v) { return __uint_as_float((unsigned)(v & 0xffffffffull)); }
+__device__ __forceinline__ float hi(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// 8-byte aligned pair in shared or global memory
+__device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
+__device__ __forceinline__ void st2(float* p, f2 v) { *reinterpret_cast<f2*>(p) = v; }
+// global pair whose high point may lie past the grid's x end (then read as 0 / not written)
+__device__ __forceinline__ f2 ld2g(const float* p, bool both) { return both ? ld2(p) : pk(p[0], 0.f); }
+__device__ __forceinline__ void st2g(float* p, f2 v, bool both) {
+    if (both)
+        st2(p, v);
+    else
+        p[0] = lo(v);
+}
+// store the points whose bit is set in m (bit 0: low, bit 1: high)
+__device__ __forceinline__ void st2m(float* p, f2 v, unsigned m) {
+    if (m == 3u)
+        st2(p, v);
+    else if (m == 1u)
+        p[0] = lo(v);
+    else if (m == 2u)
+        p[1] = hi(v);
+}
+
+struct P3 {
+    f2 x, y, z;
+};
+
+// update masks of a pair of points (gx0, gx0 + 1) on row gy: per point p, bits
+// 6p + {0, 1, 2} for Bx, By, Bz and 6p + {3, 4, 5} for Ex, Ey, Ez (x / y walls)
+__device__ __forceinline__ unsigned masks_of(const Params& P, int gx0, int gy) {
+    const bool hvy = P.per[1] || gy < P.n[1], iny = P.per[1] || (gy >= 1 && gy <= P.n[1] - 1);
+    unsigned m = 0;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int gx = gx0 + p;
+        const bool hvx = P.per[0] || gx < P.n[0], inx = P.per[0] || (gx >= 1 && gx <= P.n[0] - 1);
+        const unsigned b = (unsigned)(inx && hvy) | (unsigned)(hvx && iny) << 1 | (unsigned)(hvx && hvy) << 2 |
+                           (unsigned)(hvx && iny) << 3 | (unsigned)(inx && hvy) << 4 | (unsigned)(inx && iny) << 5;
+        m |= b << (6 * p);
+    }
+    return m;
+}
+// bits cleared on the low z wall plane: Bz, Ex, Ey of both points
+constexpr unsigned kMaskZlo = (1u << 2 | 1u << 3 | 1u << 4) * 65u;
+// the two point bits (low, high) of mask bit `b`
+__device__ __forceinline__ unsigned mbits(unsigned m, int b) { return (m >> b & 1u) | (m >> (b + 5) & 2u); }
+// per point: m bit set -> new value, else old value
+__device__ __forceinline__ f2 sel2(f2 nv, f2 ov, unsigned m2) {
+    if (m2 == 3u) return nv;
+    return pk((m2 & 1u) ? lo(nv) : lo(ov), (m2 & 2u) ? hi(nv) : hi(ov));
+}
+
+// B^{n+1/2} before masking at the pair of box positions (j, i0), (j, i0 + 1)
+// of landed stages s0 (plane k) and s1 (plane k + 1): the curl update plus the
+// CPML memory of the staged axis sax (coefficients bB, cB; zero outside the
+// slab), whose new values come back in p0, p1 (pair order)
+__device__ __forceinline__ P3 b_pair(const Params& P, const StageBuf& s0, const StageBuf& s1, int j, int i0, int sax,
+                                     f2 bB, f2 cB, f2& p0, f2& p1) {
+    const f2 ex = ld2(&s0.e[0][j][i0]), ey = ld2(&s0.e[1][j][i0]), ez = ld2(&s0.e[2][j][i0]);
+    const f2 dEz_y = sub2(ld2(&s0.e[2][j + 1][i0]), ez), dEx_y = sub2(ld2(&s0.e[0][j + 1][i0]), ex);
+    const f2 dEy_z = sub2(ld2(&s1.e[1][j][i0]), ey), dEx_z = sub2(ld2(&s1.e[0][j][i0]), ex);
+    const f2 dEz_x = sub2(pk(hi(ez), s0.e[2][j][i0 + 2]), ez), dEy_x = sub2(pk(hi(ey), s0.e[1][j][i0 + 2]), ey);
+    const f2 r0 = pk(P.r[0], P.r[0]), r1 = pk(P.r[1], P.r[1]), r2 = pk(P.r[2], P.r[2]);
+    P3 b;
+    // Bx - (r1 dEz/dy - r2 dEy/dz), By - (r2 dEx/dz - r0 dEz/dx), Bz - (r0 dEy/dx - r1 dEx/dy)
+    b.x = fma2(r2, dEy_z, sub2(ld2(&s0.b[0][j][i0]), mul2(r1, dEz_y)));
+    b.y = fma2(r0, dEz_x, sub2(ld2(&s0.b[1][j][i0]), mul2(r2, dEx_z)));
+    b.z = fma2(r1, dEx_y, sub2(ld2(&s0.b[2][j][i0]), mul2(r0, dEy_x)));
+    p0 = 0;
+    p1 = 0;
+    if (sax == 0) {          // By, Bz
+        p0 = fma2(bB, ld2(&s0.pb[0][j][i0]), mul2(cB, dEz_x));
+        p1 = fma2(bB, ld2(&s0.pb[1][j][i0]), mul2(cB, dEy_x));
+        b.y = add2(b.y, p0);
+        b.z = sub2(b.z, p1);
+    } else if (sax == 1) {   // Bx, Bz
+        p0 = fma2(bB, ld2(&s0.pb[0][j][i0]), mul2(cB, dEz_y));
+        p1 = fma2(bB, ld2(&s0.pb[1][j][i0]), mul2(cB, dEx_y));
+        b.x = sub2(b.x, p0);
+        b.z = add2(b.z, p1);
+    } else if (sax == 2) {   // Bx, By
+        p0 = fma2(bB, ld2(&s0.pb[0][j][i0]), mul2(cB, dEy_z));
+        p1 = fma2(bB, ld2(&s0.pb[1][j][i0]), mul2(cB, dEx_z));
+        b.x = add2(b.x, p0);
+        b.y = sub2(b.y, p1);
+    }
+    return b;
 }
 
 // CPML memory of a further slab axis a at box position (j, i): old values from
@@ -383,29 +467,22 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int x0 = t.x0, y0 = t.y0, kz0 = t.kz0, nq = t.nq;
 
         // ------------------------------------------------------- columns
-        const int gx = x0 + tx;
-        const int i = tx + 4;   // x position in the E / B boxes
-        const bool hvx = P.per[0] || gx < P.n[0], inx = P.per[0] || (gx >= 1 && gx <= P.n[0] - 1);
-        int gy[kRows], o[kRows];
-        bool valid[kRows], hvy[kRows], iny[kRows];
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            gy[r] = y0 + kRows * ty + r;
-            valid[r] = gx < P.N[0] && gy[r] < P.N[1];
-            o[r] = valid[r] ? gy[r] * P.pitch + gx : 0;
-            hvy[r] = P.per[1] || gy[r] < P.n[1];
-            iny[r] = P.per[1] || (gy[r] >= 1 && gy[r] <= P.n[1] - 1);
-        }
-        const int j0 = kRows * ty + 1;   // y position of row 0 in the E / B boxes
-        // halo point of warp 0 (row y0 - 1) / lanes 0..15 of warp 1 (column x0 - 1)
-        const bool hrow = ty == 0, hcol = ty == 1 && tx < kTY;
-        const int hgx = hrow ? gx : x0 - 1, hgy = hrow ? y0 - 1 : y0 + tx;
-        const int hj = hrow ? 0 : tx + 1, hi = hrow ? i : 3;
-        const bool hhvx = P.per[0] || hgx < P.n[0], hinx = P.per[0] || (hgx >= 1 && hgx <= P.n[0] - 1);
-        const bool hhvy = P.per[1] || hgy < P.n[1], hiny = P.per[1] || (hgy >= 1 && hgy <= P.n[1] - 1);
-        const int hxw = wrap_or_out(P, 0, hgx), hyw = wrap_or_out(P, 1, hgy);
-        const bool hin = hxw >= 0 && hyw >= 0;
-        const int ho = hin ? hyw * P.pitch + hxw : 0;
+        // thread: tile row `row`, x pair (gx0, gx0 + 1).  Warp 0 also forms the
+        // halo: lanes 0..15 the row y0 - 1 (in pairs), lanes 16..31 the column
+        // x0 - 1 of rows y0 .. y0 + 15 (as the pair x0 - 2, x0 - 1)
+        const int row = 2 * ty + (tx >> 4), xi = tx & 15;
+        const int gx0 = x0 + 2 * xi, gy = y0 + row;
+        const int j = row + 1, i0 = 2 * xi + 4;   // position in the E / B boxes
+        const bool v0 = gx0 < P.N[0] && gy < P.N[1], v1 = gx0 + 1 < P.N[0] && gy < P.N[1];
+        const int o = v0 ? gy * P.pitch + gx0 : 0;
+        const unsigned m = masks_of(P, gx0, gy);
+        const bool hal = ty == 0, hrow = tx < 16;
+        const int hj = hrow ? 0 : tx - 15, hi0 = hrow ? 2 * tx + 4 : 2;
+        const int hgx0 = x0 - 4 + hi0, hgy = y0 - 1 + hj;
+        const unsigned hm = masks_of(P, hgx0, hgy);
+        // no x / y wall reaches the tile or its halo: masks only on the low z wall plane
+        const bool open = (P.per[0] || (x0 - 2 >= 1 && x0 + kSX - 1 <= P.n[0] - 1)) &&
+                          (P.per[1] || (y0 - 1 >= 1 && y0 + kSY - 1 <= P.n[1] - 1));
         // periodic seams that the TMA box cannot wrap
         const bool seam = (P.per[0] && (x0 - 4 < 0 || x0 + kEX - 4 > P.N[0])) ||
                           (P.per[1] && (y0 - 1 < 0 || y0 + kEY - 1 > P.N[1]));
@@ -430,303 +507,368 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
         };
         float4 rnext = make_float4(0.f, 0.f, 0.f, 0.f);   // records of the next item
-        V3 bprev[kRows];                                    // B^{n+1/2}(k-1) at the own points
-        float elo[kRows][2];                                // E^n on the low Mur wall
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            bprev[r].x = bprev[r].y = bprev[r].z = 0.f;
-            elo[r][0] = elo[r][1] = 0.f;
-        }
-        // the plane loop, compiled twice: items that meet a source, a Mur plane,
-        // a second CPML axis or varying mu run the full version, all others a
+        f2 bpx = 0, bpy = 0;     // B^{n+1/2}(k-1) at the own pair (z differences)
+        f2 elo0 = 0, elo1 = 0;   // E^n on the low Mur wall
+        // one plane, compiled twice: items that meet a source, a Mur plane, a
+        // second CPML axis or varying mu run the full version, all others a
         // version without that code
-        auto planes = [&](auto rare_tag) {
+        auto plane = [&](auto rare_tag, int qq) -> bool {   // false: a copy never landed
             constexpr bool kRare = decltype(rare_tag)::value;
-            for (int qq = 0; qq < nq - 1; ++qq, ++it) {
-                const int k = plane_of(P, t, qq);
-                const bool doE = t.ks + qq >= kz0;   // E update (and B store) at this plane
-                const unsigned long long g0 = seq0 + qq, g1 = g0 + 1;
-                StageBuf& s0 = stg[g0 % kStages];
-                StageBuf& s1 = stg[g1 % kStages];
-                const unsigned f = s_flag[cur][qq];
-                const float4 rec = s_rec[cur][qq];
-                const int sax = (int)((f >> kFSaxShift) & 3u) - 1;
-                const bool coef = (f & kFCoef) != 0, zlo = (f & kFZlo) != 0;
-                const unsigned sec = (f / kFSec0) & 7u;
-                float(*bn)[kBY][kBX] = bplanes[it & 1];
-                const int kq = k * PL;
-                // global reads that do not depend on the stage: issued before the wait
-                float jo[kRows][3], mc[kRows][9], pe[kRows][2];
-                float bB[kRows], cB[kRows], bE[kRows], cE[kRows];
-                bool insl[kRows];
-    #pragma unroll
-                for (int r = 0; r < kRows; ++r) {
-                    const bool own = valid[r] && doE;
-                    const int q = kq + o[r];
-    #pragma unroll
-                    for (int c = 0; c < 3; ++c) jo[r][c] = (own && (coef || rec.z > 0.f)) ? P.J[c][q] : 0.f;
-                    if (own && coef) {
-    #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            mc[r][c] = __ldg(P.ca[c] + q);
-                            mc[r][3 + c] = __ldg(P.cb[c] + q);
-                            mc[r][6 + c] = __ldg(P.cj[c] + q);
-                        }
-                    } else {
-    #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            mc[r][c] = rec.x;
-                            mc[r][3 + c] = rec.y;
-                            mc[r][6 + c] = rec.z;
-                        }
-                    }
-                    bB[r] = cB[r] = bE[r] = cE[r] = pe[r][0] = pe[r][1] = 0.f;
-                    insl[r] = false;
-                    if (sax >= 0) {
-                        const int pos = sax == 0 ? gx : sax == 1 ? gy[r] : k;
-                        insl[r] = slab_pos(P, sax, pos);
-                        if (insl[r]) {
-                            bB[r] = __ldg(P.pbB[sax] + pos);
-                            cB[r] = __ldg(P.pcB[sax] + pos);
-                            bE[r] = __ldg(P.pbE[sax] + pos);
-                            cE[r] = __ldg(P.pcE[sax] + pos);
-                            if (own) {
-                                pe[r][0] = P.psiE[pair_c1(sax)][sax][q];
-                                pe[r][1] = P.psiE[pair_c2(sax)][sax][q];
-                            }
-                        }
-                    }
+            const int k = plane_of(P, t, qq);
+            const bool doE = t.ks + qq >= kz0;   // E update (and B store) at this plane
+            const unsigned long long g0 = seq0 + qq, g1 = g0 + 1;
+            StageBuf& s0 = stg[g0 % kStages];
+            StageBuf& s1 = stg[g1 % kStages];
+            const unsigned f = s_flag[cur][qq];
+            const float4 rec = s_rec[cur][qq];
+            const int sax = (int)((f >> kFSaxShift) & 3u) - 1;
+            const bool coef = (f & kFCoef) != 0, zlo = (f & kFZlo) != 0;
+            const unsigned sec = kRare ? (f / kFSec0) & 7u : 0u;
+            const bool masked = !open || zlo;
+            const unsigned mk = zlo ? m & ~kMaskZlo : m, hmk = zlo ? hm & ~kMaskZlo : hm;
+            float(*bn)[kBY][kBX] = bplanes[it & 1];
+            const int kq = k * PL, q = kq + o;
+            const bool own = v0 && doE;
+            const bool sc = coef || rec.z > 0.f;   // Js advances somewhere on the plane
+            // global reads that do not depend on the stage: issued before the wait
+            f2 jo0 = 0, jo1 = 0, jo2 = 0;
+            if (own && sc) {
+                jo0 = ld2g(P.J[0] + q, v1);
+                jo1 = ld2g(P.J[1] + q, v1);
+                jo2 = ld2g(P.J[2] + q, v1);
+            }
+            f2 ca0, ca1, ca2, cb0, cb1, cb2, cj0, cj1, cj2;
+            if (own && coef) {
+                ca0 = ld2g(P.ca[0] + q, v1);
+                ca1 = ld2g(P.ca[1] + q, v1);
+                ca2 = ld2g(P.ca[2] + q, v1);
+                cb0 = ld2g(P.cb[0] + q, v1);
+                cb1 = ld2g(P.cb[1] + q, v1);
+                cb2 = ld2g(P.cb[2] + q, v1);
+                cj0 = ld2g(P.cj[0] + q, v1);
+                cj1 = ld2g(P.cj[1] + q, v1);
+                cj2 = ld2g(P.cj[2] + q, v1);
+            } else {
+                ca0 = ca1 = ca2 = pk(rec.x, rec.x);
+                cb0 = cb1 = cb2 = pk(rec.y, rec.y);
+                cj0 = cj1 = cj2 = pk(rec.z, rec.z);
+            }
+            // CPML memory of the staged axis: coefficients (zero outside the slab), old psi_E
+            f2 bB = 0, cB = 0, bE = 0, cE = 0, pe0 = 0, pe1 = 0, hbB = 0, hcB = 0;
+            unsigned sl = 0;   // bit p: point p inside the slab
+            if (sax >= 0) {
+                const int pos0 = sax == 0 ? gx0 : sax == 1 ? gy : k, pos1 = sax == 0 ? gx0 + 1 : pos0;
+                float a0 = 0.f, b0 = 0.f, c0 = 0.f, d0 = 0.f, a1 = 0.f, b1 = 0.f, c1 = 0.f, d1 = 0.f;
+                if (slab_pos(P, sax, pos0)) {
+                    sl |= 1u;
+                    a0 = __ldg(P.pbB[sax] + pos0);
+                    b0 = __ldg(P.pcB[sax] + pos0);
+                    c0 = __ldg(P.pbE[sax] + pos0);
+                    d0 = __ldg(P.pcE[sax] + pos0);
                 }
-                float hbB = 0.f, hcB = 0.f;
-                if ((hrow || hcol) && sax >= 0) {
-                    const int hpos = sax == 0 ? hgx : sax == 1 ? hgy : k;
-                    if (slab_pos(P, sax, hpos)) {
-                        hbB = __ldg(P.pbB[sax] + hpos);
-                        hcB = __ldg(P.pcB[sax] + hpos);
-                    }
+                if (slab_pos(P, sax, pos1)) {
+                    sl |= 2u;
+                    a1 = __ldg(P.pbB[sax] + pos1);
+                    b1 = __ldg(P.pcB[sax] + pos1);
+                    c1 = __ldg(P.pbE[sax] + pos1);
+                    d1 = __ldg(P.pcE[sax] + pos1);
                 }
-                bool ok = mbar_wait(&bar[g1 % kStages], (unsigned)((g1 / kStages) & 1));
-                if (qq == 0) ok = ok && mbar_wait(&bar[g0 % kStages], (unsigned)((g0 / kStages) & 1));
-                if (seam) {
-                    if (qq == 0) patch(s0, k, sax);
-                    const int k1 = plane_of(P, t, qq + 1);
-                    patch(s1, k1, slab_axis(slab_bits(P, t, k1)));
-                    __syncthreads();
+                bB = pk(a0, a1);
+                cB = pk(b0, b1);
+                bE = pk(c0, c1);
+                cE = pk(d0, d1);
+                if (own && sl) {
+                    pe0 = ld2g(P.psiE[pair_c1(sax)][sax] + q, v1);
+                    pe1 = ld2g(P.psiE[pair_c2(sax)][sax] + q, v1);
                 }
-
-                // ------------------------------------------------ B phase
-                V3 nb[kRows];
-    #pragma unroll
-                for (int r = 0; r < kRows; ++r) {
-                    const int j = j0 + r;
-                    const bool own = valid[r] && doE;
-                    const int q = kq + o[r];
-                    const bool ux = inx && hvy[r], uy = hvx && iny[r], uz = hvx && hvy[r] && !zlo;
-                    float p0, p1;
-                    V3 b = b_update(P, s0, s1, j, i, sax, bB[r], cB[r], p0, p1);
-                    if (own && insl[r]) {
-                        if (sax == 0 ? uy : ux) O.psiB[pair_c1(sax)][sax][q] = p0;
-                        if (sax == 2 ? uy : uz) O.psiB[pair_c2(sax)][sax][q] = p1;
+                if (hal) {
+                    const int hp0 = sax == 0 ? hgx0 : sax == 1 ? hgy : k, hp1 = sax == 0 ? hgx0 + 1 : hp0;
+                    float e0 = 0.f, e1 = 0.f, h0 = 0.f, h1 = 0.f;
+                    if (slab_pos(P, sax, hp0)) {
+                        e0 = __ldg(P.pbB[sax] + hp0);
+                        h0 = __ldg(P.pcB[sax] + hp0);
                     }
-                    if (kRare && sec) {
-    #pragma unroll 1
-                        for (int a = 0; a < 3; ++a) {
-                            if (!((sec >> a) & 1u)) continue;
-                            const int pos = a == 0 ? gx : a == 1 ? gy[r] : k;
-                            if (!valid[r] || !slab_pos(P, a, pos)) continue;
-                            float e0, e1;
-                            b_psi_extra(P, s0, s1, j, i, a, pos, q, b, e0, e1);
-                            if (own) {
-                                if (a == 0 ? uy : ux) O.psiB[pair_c1(a)][a][q] = e0;
-                                if (a == 2 ? uy : uz) O.psiB[pair_c2(a)][a][q] = e1;
-                            }
-                        }
+                    if (slab_pos(P, sax, hp1)) {
+                        e1 = __ldg(P.pbB[sax] + hp1);
+                        h1 = __ldg(P.pcB[sax] + hp1);
                     }
-                    nb[r].x = ux ? b.x : s0.b[0][j][i];
-                    nb[r].y = uy ? b.y : s0.b[1][j][i];
-                    nb[r].z = uz ? b.z : s0.b[2][j][i];
-                    bn[0][j][i] = nb[r].x;
-                    bn[1][j][i] = nb[r].y;
-                    bn[2][j][i] = nb[r].z;
-                    if (own) {
-                        O.B[0][q] = nb[r].x;
-                        O.B[1][q] = nb[r].y;
-                        O.B[2][q] = nb[r].z;
-                    }
-                }
-                if (hrow || hcol) {
-                    const bool ux = hinx && hhvy, uy = hhvx && hiny, uz = hhvx && hhvy && !zlo;
-                    float p0, p1;
-                    V3 b = b_update(P, s0, s1, hj, hi, sax, hbB, hcB, p0, p1);
-                    if (kRare && sec && hin) {
-    #pragma unroll 1
-                        for (int a = 0; a < 3; ++a) {
-                            if (!((sec >> a) & 1u)) continue;
-                            const int pos = a == 0 ? hxw : a == 1 ? hyw : k;
-                            if (slab_pos(P, a, pos)) b_psi_extra(P, s0, s1, hj, hi, a, pos, kq + ho, b, p0, p1);
-                        }
-                    }
-                    if (hrow) {
-                        bn[0][hj][hi] = ux ? b.x : s0.b[0][hj][hi];
-                    } else {
-                        bn[1][hj][hi] = uy ? b.y : s0.b[1][hj][hi];
-                    }
-                    bn[2][hj][hi] = uz ? b.z : s0.b[2][hj][hi];
-                }
-                if (qq == 1) rec_store(s_item[cur ^ 1], cur ^ 1, rnext);   // loaded during plane 0
-                // every thread is past the E phase of the plane before: its stage is free
-                if (__syncthreads_or(!ok)) {
-                    aborted = true;
-                    break;
-                }
-                if (tid == 0) {
-                    consumed = g0;
-                    pump();
-                    if (qq == 0) pend = s_item[cur ^ 1] >= 0 ? fetch() : -1;
-                }
-                if (qq == 0) rec_load(s_item[cur ^ 1], rnext);
-
-                // ------------------------------------------------ E phase
-    #pragma unroll
-                for (int r = 0; r < kRows; ++r) {
-                    const int j = j0 + r;
-                    const int q = kq + o[r];
-                    if (valid[r] && doE) {
-                        const float em0 = s0.e[0][j][i], em1 = s0.e[1][j][i], em2 = s0.e[2][j][i];
-                        const bool ux = hvx && iny[r] && !zlo, uy = inx && hvy[r] && !zlo, uz = inx && iny[r];
-                        float hx = nb[r].x, hx_zm = bprev[r].x, hx_ym = r > 0 ? nb[r - 1].x : bn[0][j - 1][i];
-                        float hy = nb[r].y, hy_zm = bprev[r].y, hy_xm = bn[1][j][i - 1];
-                        float hz = nb[r].z, hz_ym = r > 0 ? nb[r - 1].z : bn[2][j - 1][i], hz_xm = bn[2][j][i - 1];
-                        if (kRare && (f & kFImu)) {   // mu varies: 1/mu per face
-                            const int gyr = gy[r];
-                            const int km = k > 0 ? k - 1 : P.N[2] - 1;
-                            const int xm = gx > 0 ? gx - 1 : P.N[0] - 1, ym = gyr > 0 ? gyr - 1 : P.N[1] - 1;
-                            hz *= imu(P, 2, gx, gyr, k); hz_ym *= imu(P, 2, gx, ym, k); hz_xm *= imu(P, 2, xm, gyr, k);
-                            hy *= imu(P, 1, gx, gyr, k); hy_zm *= imu(P, 1, gx, gyr, km); hy_xm *= imu(P, 1, xm, gyr, k);
-                            hx *= imu(P, 0, gx, gyr, k); hx_zm *= imu(P, 0, gx, gyr, km); hx_ym *= imu(P, 0, gx, ym, k);
-                        } else if (!P.uniform_mu) {   // one record: one mu
-                            hz *= rec.w; hz_ym *= rec.w; hz_xm *= rec.w; hy *= rec.w; hy_zm *= rec.w;
-                            hy_xm *= rec.w; hx *= rec.w; hx_zm *= rec.w; hx_ym *= rec.w;
-                        }
-                        const float dHz_y = hz - hz_ym, dHy_z = hy - hy_zm;
-                        const float dHx_z = hx - hx_zm, dHz_x = hz - hz_xm;
-                        const float dHy_x = hy - hy_xm, dHx_y = hx - hx_ym;
-                        float cx = P.r[1] * dHz_y - P.r[2] * dHy_z;
-                        float cy = P.r[2] * dHx_z - P.r[0] * dHz_x;
-                        float cz = P.r[0] * dHy_x - P.r[1] * dHx_y;
-                        // CPML memory: psi' = b psi + c d, added to the curl
-                        float p0 = 0.f, p1 = 0.f;
-                        if (sax == 0) {          // Ey, Ez
-                            p0 = bE[r] * pe[r][0] + cE[r] * dHz_x;
-                            p1 = bE[r] * pe[r][1] + cE[r] * dHy_x;
-                            cy -= p0;
-                            cz += p1;
-                        } else if (sax == 1) {   // Ex, Ez
-                            p0 = bE[r] * pe[r][0] + cE[r] * dHz_y;
-                            p1 = bE[r] * pe[r][1] + cE[r] * dHx_y;
-                            cx += p0;
-                            cz -= p1;
-                        } else if (sax == 2) {   // Ex, Ey
-                            p0 = bE[r] * pe[r][0] + cE[r] * dHy_z;
-                            p1 = bE[r] * pe[r][1] + cE[r] * dHx_z;
-                            cx -= p0;
-                            cy += p1;
-                        }
-                        if (insl[r]) {
-                            if (sax == 0 ? uy : ux) P.psiE[pair_c1(sax)][sax][q] = p0;
-                            if (sax == 2 ? uy : uz) P.psiE[pair_c2(sax)][sax][q] = p1;
-                        }
-                        if (kRare && sec) {
-    #pragma unroll 1
-                            for (int a = 0; a < 3; ++a) {
-                                if (!((sec >> a) & 1u)) continue;
-                                const int pos = a == 0 ? gx : a == 1 ? gy[r] : k;
-                                if (!slab_pos(P, a, pos)) continue;
-                                const float bb = __ldg(P.pbE[a] + pos), cc = __ldg(P.pcE[a] + pos);
-                                float* q1 = P.psiE[pair_c1(a)][a] + q;
-                                float* q2 = P.psiE[pair_c2(a)][a] + q;
-                                const float o1 = *q1, o2 = *q2;
-                                if (a == 0) {
-                                    const float n1 = bb * o1 + cc * dHz_x, n2 = bb * o2 + cc * dHy_x;
-                                    cy -= n1;
-                                    cz += n2;
-                                    if (uy) *q1 = n1;
-                                    if (uz) *q2 = n2;
-                                } else if (a == 1) {
-                                    const float n1 = bb * o1 + cc * dHz_y, n2 = bb * o2 + cc * dHx_y;
-                                    cx += n1;
-                                    cz -= n2;
-                                    if (ux) *q1 = n1;
-                                    if (uz) *q2 = n2;
-                                } else {
-                                    const float n1 = bb * o1 + cc * dHy_z, n2 = bb * o2 + cc * dHx_z;
-                                    cx -= n1;
-                                    cy += n2;
-                                    if (ux) *q1 = n1;
-                                    if (uy) *q2 = n2;
-                                }
-                            }
-                        }
-                        float jt0 = 0.f, jt1 = 0.f, jt2 = 0.f;
-                        if (mc[r][6] > 0.f && ux) {
-                            jt0 = jo[r][0] + mc[r][6] * em0;
-                            P.J[0][q] = jt0;
-                        }
-                        if (mc[r][7] > 0.f && uy) {
-                            jt1 = jo[r][1] + mc[r][7] * em1;
-                            P.J[1][q] = jt1;
-                        }
-                        if (mc[r][8] > 0.f && uz) {
-                            jt2 = jo[r][2] + mc[r][8] * em2;
-                            P.J[2][q] = jt2;
-                        }
-                        float n0 = mc[r][0] * em0 + mc[r][3] * (cx - jt0);
-                        float n1 = mc[r][1] * em1 + mc[r][4] * (cy - jt1);
-                        float n2 = mc[r][2] * em2 + mc[r][5] * (cz - jt2);
-                        if (kRare && (f & kFSrc)) {
-                            const int gyr = gy[r];
-                            for (int s = 0; s < S.n; ++s) {
-                                if (gx >= S.lo[s][0] && gx < S.hi[s][0] && gyr >= S.lo[s][1] && gyr < S.hi[s][1] &&
-                                    k >= S.lo[s][2] && k < S.hi[s][2]) {
-                                    if (S.comp[s] == 0) n0 += S.amp[s];
-                                    if (S.comp[s] == 1) n1 += S.amp[s];
-                                    if (S.comp[s] == 2) n2 += S.amp[s];
-                                }
-                            }
-                        }
-                        n0 = ux ? n0 : em0;
-                        n1 = uy ? n1 : em1;
-                        n2 = uz ? n2 : em2;
-                        O.E[0][q] = n0;
-                        O.E[1][q] = n1;
-                        O.E[2][q] = n2;
-                        if (!isfinite(n0 + n1 + n2)) atomicOr(P.status, kStatusNonFinite);
-                        // first-order Mur on the z walls: E_w^{n+1} = E_i^n + M (E_i^{n+1} - E_w^n)
-                        if (kRare && (f & (kFMurLo | kFMurHi))) {
-                            const bool mx = hvx && iny[r], my = inx && hvy[r];
-                            if (f & kFMurLo) {
-                                if (mx) O.E[0][o[r]] = em0 + P.mur_M * (n0 - elo[r][0]);
-                                if (my) O.E[1][o[r]] = em1 + P.mur_M * (n1 - elo[r][1]);
-                            }
-                            if (f & kFMurHi) {
-                                const int pw = P.n[2] * PL + o[r];
-                                if (mx) O.E[0][pw] = em0 + P.mur_M * (n0 - s1.e[0][j][i]);
-                                if (my) O.E[1][pw] = em1 + P.mur_M * (n1 - s1.e[1][j][i]);
-                            }
-                        }
-                    }
-                    if (kRare && zlo) {
-                        elo[r][0] = s0.e[0][j][i];
-                        elo[r][1] = s0.e[1][j][i];
-                    }
-                    bprev[r] = nb[r];
+                    hbB = pk(e0, e1);
+                    hcB = pk(h0, h1);
                 }
             }
+            bool ok = mbar_wait(&bar[g1 % kStages], (unsigned)((g1 / kStages) & 1));
+            if (qq == 0) ok = ok && mbar_wait(&bar[g0 % kStages], (unsigned)((g0 / kStages) & 1));
+            if (seam) {
+                if (qq == 0) patch(s0, k, sax);
+                const int k1 = plane_of(P, t, qq + 1);
+                patch(s1, k1, slab_axis(slab_bits(P, t, k1)));
+                __syncthreads();
+            }
+
+            // ------------------------------------------------ B phase
+            f2 p0, p1;
+            P3 nb = b_pair(P, s0, s1, j, i0, sax, bB, cB, p0, p1);
+            if (kRare && sec) {   // CPML memory of further slab axes, point by point
+                V3 b[2] = {{lo(nb.x), lo(nb.y), lo(nb.z)}, {hi(nb.x), hi(nb.y), hi(nb.z)}};
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    if (!(p ? v1 : v0)) continue;
+#pragma unroll 1
+                    for (int a = 0; a < 3; ++a) {
+                        if (!((sec >> a) & 1u)) continue;
+                        const int pos = a == 0 ? gx0 + p : a == 1 ? gy : k;
+                        if (!slab_pos(P, a, pos)) continue;
+                        float e0, e1;
+                        b_psi_extra(P, s0, s1, j, i0 + p, a, pos, q + p, b[p], e0, e1);
+                        if (own) {
+                            if (mk >> (6 * p + pair_c1(a)) & 1u) O.psiB[pair_c1(a)][a][q + p] = e0;
+                            if (mk >> (6 * p + pair_c2(a)) & 1u) O.psiB[pair_c2(a)][a][q + p] = e1;
+                        }
+                    }
+                }
+                nb.x = pk(b[0].x, b[1].x);
+                nb.y = pk(b[0].y, b[1].y);
+                nb.z = pk(b[0].z, b[1].z);
+            }
+            if (masked) {
+                nb.x = sel2(nb.x, ld2(&s0.b[0][j][i0]), mbits(mk, 0));
+                nb.y = sel2(nb.y, ld2(&s0.b[1][j][i0]), mbits(mk, 1));
+                nb.z = sel2(nb.z, ld2(&s0.b[2][j][i0]), mbits(mk, 2));
+            }
+            st2(&bn[0][j][i0], nb.x);
+            st2(&bn[1][j][i0], nb.y);
+            st2(&bn[2][j][i0], nb.z);
+            if (own) {
+                st2g(O.B[0] + q, nb.x, v1);
+                st2g(O.B[1] + q, nb.y, v1);
+                st2g(O.B[2] + q, nb.z, v1);
+                if (sl) {
+                    const unsigned vm = v1 ? 3u : 1u;
+                    st2m(O.psiB[pair_c1(sax)][sax] + q, p0, sl & vm & mbits(mk, pair_c1(sax)));
+                    st2m(O.psiB[pair_c2(sax)][sax] + q, p1, sl & vm & mbits(mk, pair_c2(sax)));
+                }
+            }
+            if (hal) {
+                f2 hp0, hp1;
+                P3 h = b_pair(P, s0, s1, hj, hi0, sax, hbB, hcB, hp0, hp1);
+                if (kRare && sec) {
+                    V3 b[2] = {{lo(h.x), lo(h.y), lo(h.z)}, {hi(h.x), hi(h.y), hi(h.z)}};
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        const int xw = wrap_or_out(P, 0, hgx0 + p), yw = wrap_or_out(P, 1, hgy);
+                        if (xw < 0 || yw < 0) continue;
+#pragma unroll 1
+                        for (int a = 0; a < 3; ++a) {
+                            if (!((sec >> a) & 1u)) continue;
+                            const int pos = a == 0 ? xw : a == 1 ? yw : k;
+                            float e0, e1;   // new halo memory: formed by the owner
+                            if (slab_pos(P, a, pos))
+                                b_psi_extra(P, s0, s1, hj, hi0 + p, a, pos, kq + yw * P.pitch + xw, b[p], e0, e1);
+                        }
+                    }
+                    h.x = pk(b[0].x, b[1].x);
+                    h.y = pk(b[0].y, b[1].y);
+                    h.z = pk(b[0].z, b[1].z);
+                }
+                if (masked) {
+                    h.x = sel2(h.x, ld2(&s0.b[0][hj][hi0]), mbits(hmk, 0));
+                    h.y = sel2(h.y, ld2(&s0.b[1][hj][hi0]), mbits(hmk, 1));
+                    h.z = sel2(h.z, ld2(&s0.b[2][hj][hi0]), mbits(hmk, 2));
+                }
+                if (hrow)
+                    st2(&bn[0][hj][hi0], h.x);
+                else
+                    st2(&bn[1][hj][hi0], h.y);
+                st2(&bn[2][hj][hi0], h.z);
+            }
+            if (qq == 1) rec_store(s_item[cur ^ 1], cur ^ 1, rnext);   // loaded during plane 0
+            // every thread is past the E phase of the plane before: its stage is free
+            if (__syncthreads_or(!ok)) return false;
+            if (tid == 0) {
+                consumed = g0;
+                pump();
+                if (qq == 0) pend = s_item[cur ^ 1] >= 0 ? fetch() : -1;
+            }
+            if (qq == 0) rec_load(s_item[cur ^ 1], rnext);
+
+            // ------------------------------------------------ E phase
+            if (own) {
+                const f2 em0 = ld2(&s0.e[0][j][i0]), em1 = ld2(&s0.e[1][j][i0]), em2 = ld2(&s0.e[2][j][i0]);
+                f2 hx = nb.x, hx_zm = bpx, hx_ym = ld2(&bn[0][j - 1][i0]);
+                f2 hy = nb.y, hy_zm = bpy, hy_xm = pk(bn[1][j][i0 - 1], lo(nb.y));
+                f2 hz = nb.z, hz_ym = ld2(&bn[2][j - 1][i0]), hz_xm = pk(bn[2][j][i0 - 1], lo(nb.z));
+                const bool imuf = kRare && (f & kFImu);
+                if (!P.uniform_mu && !imuf) {   // one record: one mu
+                    const f2 w = pk(rec.w, rec.w);
+                    hx = mul2(hx, w); hx_zm = mul2(hx_zm, w); hx_ym = mul2(hx_ym, w);
+                    hy = mul2(hy, w); hy_zm = mul2(hy_zm, w); hy_xm = mul2(hy_xm, w);
+                    hz = mul2(hz, w); hz_ym = mul2(hz_ym, w); hz_xm = mul2(hz_xm, w);
+                }
+                f2 dHz_y = sub2(hz, hz_ym), dHy_z = sub2(hy, hy_zm), dHx_z = sub2(hx, hx_zm);
+                f2 dHz_x = sub2(hz, hz_xm), dHy_x = sub2(hy, hy_xm), dHx_y = sub2(hx, hx_ym);
+                if (imuf) {   // mu varies: 1/mu per face, point by point
+                    float d[6][2];
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        const int gx = gx0 + p;
+                        const int km = k > 0 ? k - 1 : P.N[2] - 1;
+                        const int xm = gx > 0 ? gx - 1 : P.N[0] - 1, ym = gy > 0 ? gy - 1 : P.N[1] - 1;
+                        auto h = [&](f2 v) { return p ? hi(v) : lo(v); };
+                        const bool vp = p ? v1 : v0;
+                        const int gxs = vp ? gx : gx0, xms = vp ? xm : gx0;
+                        const float Hz = h(hz) * imu(P, 2, gxs, gy, k), Hz_ym = h(hz_ym) * imu(P, 2, gxs, ym, k);
+                        const float Hz_xm = h(hz_xm) * imu(P, 2, xms, gy, k);
+                        const float Hy = h(hy) * imu(P, 1, gxs, gy, k), Hy_zm = h(hy_zm) * imu(P, 1, gxs, gy, km);
+                        const float Hy_xm = h(hy_xm) * imu(P, 1, xms, gy, k);
+                        const float Hx = h(hx) * imu(P, 0, gxs, gy, k), Hx_zm = h(hx_zm) * imu(P, 0, gxs, gy, km);
+                        const float Hx_ym = h(hx_ym) * imu(P, 0, gxs, ym, k);
+                        d[0][p] = Hz - Hz_ym;
+                        d[1][p] = Hy - Hy_zm;
+                        d[2][p] = Hx - Hx_zm;
+                        d[3][p] = Hz - Hz_xm;
+                        d[4][p] = Hy - Hy_xm;
+                        d[5][p] = Hx - Hx_ym;
+                    }
+                    dHz_y = pk(d[0][0], d[0][1]);
+                    dHy_z = pk(d[1][0], d[1][1]);
+                    dHx_z = pk(d[2][0], d[2][1]);
+                    dHz_x = pk(d[3][0], d[3][1]);
+                    dHy_x = pk(d[4][0], d[4][1]);
+                    dHx_y = pk(d[5][0], d[5][1]);
+                }
+                const f2 r0 = pk(P.r[0], P.r[0]), r1 = pk(P.r[1], P.r[1]), r2 = pk(P.r[2], P.r[2]);
+                f2 cx = sub2(mul2(r1, dHz_y), mul2(r2, dHy_z));
+                f2 cy = sub2(mul2(r2, dHx_z), mul2(r0, dHz_x));
+                f2 cz = sub2(mul2(r0, dHy_x), mul2(r1, dHx_y));
+                // CPML memory of the staged axis: psi' = b psi + c d, added to the curl
+                f2 q0 = 0, q1 = 0;
+                if (sax == 0) {          // Ey, Ez
+                    q0 = fma2(bE, pe0, mul2(cE, dHz_x));
+                    q1 = fma2(bE, pe1, mul2(cE, dHy_x));
+                    cy = sub2(cy, q0);
+                    cz = add2(cz, q1);
+                } else if (sax == 1) {   // Ex, Ez
+                    q0 = fma2(bE, pe0, mul2(cE, dHz_y));
+                    q1 = fma2(bE, pe1, mul2(cE, dHx_y));
+                    cx = add2(cx, q0);
+                    cz = sub2(cz, q1);
+                } else if (sax == 2) {   // Ex, Ey
+                    q0 = fma2(bE, pe0, mul2(cE, dHy_z));
+                    q1 = fma2(bE, pe1, mul2(cE, dHx_z));
+                    cx = sub2(cx, q0);
+                    cy = add2(cy, q1);
+                }
+                if (kRare && sec) {   // further slab axes, point by point
+                    float c3[3][2] = {{lo(cx), hi(cx)}, {lo(cy), hi(cy)}, {lo(cz), hi(cz)}};
+                    const f2 dh[6] = {dHz_x, dHy_x, dHz_y, dHx_y, dHy_z, dHx_z};   // pair order of axes 0, 1, 2
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        if (!(p ? v1 : v0)) continue;
+#pragma unroll 1
+                        for (int a = 0; a < 3; ++a) {
+                            if (!((sec >> a) & 1u)) continue;
+                            const int pos = a == 0 ? gx0 + p : a == 1 ? gy : k;
+                            if (!slab_pos(P, a, pos)) continue;
+                            const float bb = __ldg(P.pbE[a] + pos), cc = __ldg(P.pcE[a] + pos);
+                            const int c1 = pair_c1(a), c2 = pair_c2(a);
+                            float* w1 = P.psiE[c1][a] + q + p;
+                            float* w2 = P.psiE[c2][a] + q + p;
+                            const float d1 = p ? hi(dh[2 * a]) : lo(dh[2 * a]);
+                            const float d2 = p ? hi(dh[2 * a + 1]) : lo(dh[2 * a + 1]);
+                            const float n1 = bb * *w1 + cc * d1, n2 = bb * *w2 + cc * d2;
+                            // the pair (c1, c2) of axis a enters the curl with signs (-, +), (+, -), (-, +)
+                            const float s = a == 1 ? 1.f : -1.f;
+                            c3[c1][p] += s * n1;
+                            c3[c2][p] -= s * n2;
+                            if (mk >> (6 * p + 3 + c1) & 1u) *w1 = n1;
+                            if (mk >> (6 * p + 3 + c2) & 1u) *w2 = n2;
+                        }
+                    }
+                    cx = pk(c3[0][0], c3[0][1]);
+                    cy = pk(c3[1][0], c3[1][1]);
+                    cz = pk(c3[2][0], c3[2][1]);
+                }
+                // Js^{n+1/2} = Js + kt E^n, E^{n+1} = ca E^n + cb (curl - Js^{n+1/2})
+                f2 jt0 = 0, jt1 = 0, jt2 = 0;
+                if (sc) {
+                    jt0 = fma2(cj0, em0, jo0);
+                    jt1 = fma2(cj1, em1, jo1);
+                    jt2 = fma2(cj2, em2, jo2);
+                }
+                f2 n0 = fma2(cb0, sub2(cx, jt0), mul2(ca0, em0));
+                f2 n1 = fma2(cb1, sub2(cy, jt1), mul2(ca1, em1));
+                f2 n2 = fma2(cb2, sub2(cz, jt2), mul2(ca2, em2));
+                if (kRare && (f & kFSrc)) {   // soft sources, point by point
+                    float e3[3][2] = {{lo(n0), hi(n0)}, {lo(n1), hi(n1)}, {lo(n2), hi(n2)}};
+                    for (int s = 0; s < S.n; ++s) {
+                        if (gy < S.lo[s][1] || gy >= S.hi[s][1] || k < S.lo[s][2] || k >= S.hi[s][2]) continue;
+                        const int c = S.comp[s];
+#pragma unroll
+                        for (int p = 0; p < 2; ++p)
+                            if (gx0 + p >= S.lo[s][0] && gx0 + p < S.hi[s][0]) e3[c][p] += S.amp[s];
+                    }
+                    n0 = pk(e3[0][0], e3[0][1]);
+                    n1 = pk(e3[1][0], e3[1][1]);
+                    n2 = pk(e3[2][0], e3[2][1]);
+                }
+                if (masked) {
+                    n0 = sel2(n0, em0, mbits(mk, 3));
+                    n1 = sel2(n1, em1, mbits(mk, 4));
+                    n2 = sel2(n2, em2, mbits(mk, 5));
+                    jt0 = sel2(jt0, jo0, mbits(mk, 3));
+                    jt1 = sel2(jt1, jo1, mbits(mk, 4));
+                    jt2 = sel2(jt2, jo2, mbits(mk, 5));
+                }
+                st2g(O.E[0] + q, n0, v1);
+                st2g(O.E[1] + q, n1, v1);
+                st2g(O.E[2] + q, n2, v1);
+                if (sc) {
+                    st2g(P.J[0] + q, jt0, v1);
+                    st2g(P.J[1] + q, jt1, v1);
+                    st2g(P.J[2] + q, jt2, v1);
+                }
+                if (sl) {
+                    const unsigned vm = v1 ? 3u : 1u;
+                    st2m(P.psiE[pair_c1(sax)][sax] + q, q0, sl & vm & mbits(mk, 3 + pair_c1(sax)));
+                    st2m(P.psiE[pair_c2(sax)][sax] + q, q1, sl & vm & mbits(mk, 3 + pair_c2(sax)));
+                }
+                const f2 sum = add2(add2(n0, n1), n2);
+                if (!isfinite(lo(sum) + (v1 ? hi(sum) : 0.f))) atomicOr(P.status, kStatusNonFinite);
+                // first-order Mur on the z walls: E_w^{n+1} = E_i^n + M (E_i^{n+1} - E_w^n)
+                if (kRare && (f & (kFMurLo | kFMurHi))) {
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        if (!(p ? v1 : v0)) continue;
+                        auto h = [&](f2 v) { return p ? hi(v) : lo(v); };
+                        const bool mx = m >> (6 * p + 3) & 1u, my = m >> (6 * p + 4) & 1u;
+                        const int ow = o + p, pw = P.n[2] * PL + o + p;
+                        if (f & kFMurLo) {
+                            if (mx) O.E[0][ow] = h(em0) + P.mur_M * (h(n0) - h(elo0));
+                            if (my) O.E[1][ow] = h(em1) + P.mur_M * (h(n1) - h(elo1));
+                        }
+                        if (f & kFMurHi) {
+                            if (mx) O.E[0][pw] = h(em0) + P.mur_M * (h(n0) - s1.e[0][j][i0 + p]);
+                            if (my) O.E[1][pw] = h(em1) + P.mur_M * (h(n1) - s1.e[1][j][i0 + p]);
+                        }
+                    }
+                }
+            }
+            if (kRare && zlo) {
+                elo0 = ld2(&s0.e[0][j][i0]);
+                elo1 = ld2(&s0.e[1][j][i0]);
+            }
+            bpx = nb.x;
+            bpy = nb.y;
+            return true;
         };
-        if (item_is_rare(P, S, mur, t))
-            planes(std::true_type{});
-        else
-            planes(std::false_type{});
+        const bool rare = item_is_rare(P, S, mur, t);
+        for (int qq = 0; qq < nq - 1; ++qq, ++it) {
+            const bool ok = rare ? plane(std::true_type{}, qq) : plane(std::false_type{}, qq);
+            if (!ok) {
+                aborted = true;
+                break;
+            }
+        }
         if (aborted) break;
         seq0 += nq;
         // this item is done: its slot takes the item after the next one
