@@ -193,9 +193,10 @@ def algorithmic_bytes(w, N):
 
 
 def source_hash():
+    """Hash of the sources that define the step kernel (its file and the shared header)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2305_13419_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for f in ("tf_step.cu", "tf_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2305_13419_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -186,6 +186,24 @@ tf_status tf_read_probe_series(tf_handle h, int id, double* out, int64_t n);
  * float32 into a host or device buffer.  Synchronises the stream. */
 tf_status tf_read_field(tf_handle h, int comp, float* dst, int on_device);
 
+/* Checkpoint of the time-stepping state, so that a run of Algorithm 1 (the
+ * paper's resonator runs take 10^5 - 10^6 steps, Sec. 5) can stop and resume
+ * bit-identically.  The blob holds a header (grid sizes, level, priming
+ * state), E, B, Js at the level the state holds them, the CPML memories and
+ * the probe DFT accumulators and series.  It does not hold the
+ * configuration: materials, sources and probe definitions must be set on the
+ * handle before tf_checkpoint_load exactly as they were when the blob was
+ * saved (the header checks sizes, boundary layout, probe count and dt).
+ *   tf_checkpoint_size  bytes of a blob for this handle;
+ *   tf_checkpoint_save  writes the blob to dst (host memory, or device memory
+ *                       when on_device != 0); bytes >= tf_checkpoint_size;
+ *   tf_checkpoint_load  restores the state from src; TF_EINVAL when the
+ *                       header does not match this handle.
+ * The caller owns dst / src.  Both synchronise the stream. */
+tf_status tf_checkpoint_size(tf_handle h, size_t* bytes);
+tf_status tf_checkpoint_save(tf_handle h, void* dst, size_t bytes, int on_device);
+tf_status tf_checkpoint_load(tf_handle h, const void* src, size_t bytes, int on_device);
+
 /* Q-factor of one damped mode from probe id's DFT (Sec. 5 reports Q and the
  * resonance from the ring-down): fits X_k = dt sum_{n0<=n<N} (a z^n + c.c.)
  * w_k^n, z = exp((-alpha + i omega0) dt), in FP64 on the GPU.  f_guess and

@@ -635,6 +635,148 @@ tf_status tf_read_field(tf_handle h, int comp, float* dst, int on_device) {
     return TF_OK;
 }
 
+// ------------------------------------------------------------- checkpoints
+namespace {
+
+constexpr size_t kCkptHeader = 256;
+
+struct CkptHeader {
+    char magic[8];
+    int32_t N[3], pitch, bc[3], ncpml_axes, nprobes, max_probes;
+    int64_t series_cap, level;
+    int32_t primed, reserved;
+    double dt;
+    uint64_t field_bytes, total_bytes;
+};
+static_assert(sizeof(CkptHeader) <= kCkptHeader, "checkpoint header");
+
+const char kCkptMagic[8] = {'T', 'F', 'C', 'K', 'P', 'T', '1', 0};
+
+// the arrays of a blob after the header, in order: E, B, Js at the level the
+// state holds them; per CPML axis the psi_B pair and the psi_E pair; the
+// probe DFT accumulators; the probe series.  `cur` gives the arrays the state
+// is read from / written to, `other` the second buffer of ping-pong arrays
+// (nullptr where there is none)
+struct CkptPart {
+    float* cur;
+    float* other;
+    size_t bytes;
+};
+
+int ckpt_parts(const tf_ctx* h, CkptPart* parts) {
+    const size_t fb = sizeof(float) * (size_t)h->L.total;
+    int n = 0;
+    for (int c = 0; c < 3; ++c) parts[n++] = {h->P.E[c], h->O.E[c], fb};
+    for (int c = 0; c < 3; ++c) parts[n++] = {h->P.B[c], h->O.B[c], fb};
+    for (int c = 0; c < 3; ++c) parts[n++] = {h->P.J[c], nullptr, fb};
+    for (int a = 0; a < 3; ++a) {
+        if (h->desc.bc[a].kind != TF_BC_CPML) continue;
+        for (int c = 0; c < 3; ++c)
+            if (c != a) parts[n++] = {h->P.psiB[c][a], h->O.psiB[c][a], fb};
+        for (int c = 0; c < 3; ++c)
+            if (c != a) parts[n++] = {h->P.psiE[c][a], nullptr, fb};
+    }
+    const size_t pb = sizeof(double) * TF_MAX_PROBES * TF_MAX_FREQS;
+    parts[n++] = {(float*)h->R.re, nullptr, pb};
+    parts[n++] = {(float*)h->R.im, nullptr, pb};
+    if (h->R.series) parts[n++] = {(float*)h->R.series, nullptr, sizeof(double) * (size_t)h->desc.max_probes * h->R.cap};
+    return n;
+}
+
+size_t ckpt_bytes(const tf_ctx* h) {
+    CkptPart parts[40];
+    const int n = ckpt_parts(h, parts);
+    size_t b = kCkptHeader;
+    for (int k = 0; k < n; ++k) b += parts[k].bytes;
+    return b;
+}
+
+CkptHeader ckpt_header(const tf_ctx* h) {
+    CkptHeader H;
+    memset(&H, 0, sizeof(H));
+    memcpy(H.magic, kCkptMagic, sizeof(kCkptMagic));
+    for (int a = 0; a < 3; ++a) {
+        H.N[a] = h->L.N[a];
+        H.bc[a] = h->desc.bc[a].kind;
+    }
+    H.pitch = h->L.pitch;
+    H.ncpml_axes = h->L.ncpml_axes;
+    H.nprobes = h->R.n;
+    H.max_probes = h->desc.max_probes;
+    H.series_cap = h->R.cap;
+    H.level = h->level;
+    H.primed = h->primed;
+    H.dt = h->dt;
+    H.field_bytes = sizeof(float) * (uint64_t)h->L.total;
+    H.total_bytes = ckpt_bytes(h);
+    return H;
+}
+
+}  // namespace
+
+tf_status tf_checkpoint_size(tf_handle h, size_t* bytes) {
+    if (!h || !bytes) return TF_EINVAL;
+    *bytes = ckpt_bytes(h);
+    return TF_OK;
+}
+
+tf_status tf_checkpoint_save(tf_handle h, void* dst, size_t bytes, int on_device) {
+    if (!h || !dst || bytes < ckpt_bytes(h)) return TF_EINVAL;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    char* d = (char*)dst;
+    const CkptHeader H = ckpt_header(h);
+    if (on_device) {
+        TF_CUDA(cudaMemcpyAsync(d, &H, sizeof(H), cudaMemcpyHostToDevice, h->stream));
+    } else {
+        memset(d, 0, kCkptHeader);
+        memcpy(d, &H, sizeof(H));
+    }
+    CkptPart parts[40];
+    const int n = ckpt_parts(h, parts);
+    size_t o = kCkptHeader;
+    for (int k = 0; k < n; ++k) {
+        TF_CUDA(cudaMemcpyAsync(d + o, parts[k].cur, parts[k].bytes, kind, h->stream));
+        o += parts[k].bytes;
+    }
+    TF_CUDA(cudaStreamSynchronize(h->stream));
+    return TF_OK;
+}
+
+tf_status tf_checkpoint_load(tf_handle h, const void* src, size_t bytes, int on_device) {
+    if (!h || !src || bytes < kCkptHeader) return TF_EINVAL;
+    const char* s = (const char*)src;
+    CkptHeader H;
+    if (on_device) {
+        TF_CUDA(cudaMemcpyAsync(&H, s, sizeof(H), cudaMemcpyDeviceToHost, h->stream));
+        TF_CUDA(cudaStreamSynchronize(h->stream));
+    } else {
+        memcpy(&H, s, sizeof(H));
+    }
+    CkptHeader M = ckpt_header(h);
+    bool same = memcmp(H.magic, M.magic, sizeof(H.magic)) == 0 && H.pitch == M.pitch &&
+                H.ncpml_axes == M.ncpml_axes && H.nprobes == M.nprobes && H.max_probes == M.max_probes &&
+                H.series_cap == M.series_cap && H.dt == M.dt && H.field_bytes == M.field_bytes &&
+                H.total_bytes == M.total_bytes && bytes >= M.total_bytes;
+    for (int a = 0; a < 3; ++a) same = same && H.N[a] == M.N[a] && H.bc[a] == M.bc[a];
+    if (!same || (H.primed != 0 && H.primed != 1) || H.level < 0) return TF_EINVAL;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CkptPart parts[40];
+    const int n = ckpt_parts(h, parts);
+    size_t o = kCkptHeader;
+    for (int k = 0; k < n; ++k) {
+        TF_CUDA(cudaMemcpyAsync(parts[k].cur, s + o, parts[k].bytes, kind, h->stream));
+        // the second buffer of a ping-pong array holds the same values, so that
+        // points the step never writes (walls) agree in both
+        if (parts[k].other) TF_CUDA(cudaMemcpyAsync(parts[k].other, s + o, parts[k].bytes, kind, h->stream));
+        o += parts[k].bytes;
+    }
+    TF_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    TF_CUDA(cudaStreamSynchronize(h->stream));
+    h->level = H.level;
+    h->primed = H.primed;
+    return TF_OK;
+}
+
 tf_status tf_field_stats(tf_handle h, int comp, double* sumsq, double* maxabs, int64_t* nonfinite) {
     if (!h || comp < 0 || comp > 8) return TF_EINVAL;
     const float* f = comp < 3 ? h->P.E[comp] : comp < 6 ? h->P.B[comp - 3] : h->P.J[comp - 6];

@@ -26,7 +26,8 @@ TF_MAX_PROBES, TF_MAX_FREQS, TF_MAX_SOURCES = 16, 64, 16
 EXPORTS = ["tf_workspace_size", "tf_create", "tf_destroy", "tf_storage_dims", "tf_get_time", "tf_get_dt",
            "tf_set_materials", "tf_set_field", "tf_add_source", "tf_add_probe", "tf_step", "tf_sync",
            "tf_read_probe_dft", "tf_read_probe_series", "tf_read_field", "tf_fit_q", "tf_strerror",
-           "tf_step_timed", "tf_field_stats", "tf_field_stats_noalloc"]
+           "tf_step_timed", "tf_field_stats", "tf_field_stats_noalloc", "tf_checkpoint_size",
+           "tf_checkpoint_save", "tf_checkpoint_load"]
 
 
 class TFError(RuntimeError):
@@ -87,7 +88,10 @@ def load(build_if_missing: bool = True):
                        ("tf_fit_q", [vp, C.c_int, C.c_double, C.c_double, dp, dp, dp]),
                        ("tf_field_stats", [vp, C.c_int, dp, dp, C.POINTER(C.c_int64)]),
                        ("tf_field_stats_noalloc", [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, dp, dp,
-                                                   C.POINTER(C.c_int64), vp])):
+                                                   C.POINTER(C.c_int64), vp]),
+                       ("tf_checkpoint_size", [vp, C.POINTER(C.c_size_t)]),
+                       ("tf_checkpoint_save", [vp, vp, C.c_size_t, C.c_int]),
+                       ("tf_checkpoint_load", [vp, vp, C.c_size_t, C.c_int])):
         fn = getattr(L, name)
         fn.restype = st
         fn.argtypes = args
@@ -322,6 +326,25 @@ class Grid:
         s, m, n = C.c_double(), C.c_double(), C.c_int64()
         _check(load().tf_field_stats(self.h, int(comp), C.byref(s), C.byref(m), C.byref(n)), "tf_field_stats")
         return s.value, m.value, int(n.value)
+
+    def checkpoint_size(self) -> int:
+        n = C.c_size_t()
+        _check(load().tf_checkpoint_size(self.h, C.byref(n)), "tf_checkpoint_size")
+        return int(n.value)
+
+    def save_checkpoint(self, out=None):
+        """State blob (numpy uint8, or into `out`: a uint8 host array or CUDA tensor)."""
+        if out is None:
+            out = np.empty(self.checkpoint_size(), np.uint8)
+        p, dev = _ptr(out)
+        nbytes = out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes
+        _check(load().tf_checkpoint_save(self.h, p, int(nbytes), dev), "tf_checkpoint_save")
+        return out
+
+    def load_checkpoint(self, blob):
+        p, dev = _ptr(blob)
+        nbytes = blob.numel() * blob.element_size() if hasattr(blob, "numel") else blob.nbytes
+        _check(load().tf_checkpoint_load(self.h, p, int(nbytes), dev), "tf_checkpoint_load")
 
     def fit_q(self, pid: int, f_guess: float = 0.0, q_guess: float = 100.0):
         f0, al, q = C.c_double(), C.c_double(), C.c_double()
