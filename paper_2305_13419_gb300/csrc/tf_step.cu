@@ -7,34 +7,39 @@
 //   E^{n+1}    = ca E^n + cb (curl(Bt/mu) - Jt^{n+1/2})     (step 3, CPML psi_E)
 // plus soft sources, first-order Mur z walls and the non-finite watchdog.
 //
-// Work layout.  A CTA of 32 x 8 threads owns a 32 x 16 column tile, two
-// adjacent rows per thread, and streams it along z through a chunk of planes.
-// Each plane's E^n, B^{n-1/2} and -- where a CPML slab reaches the tile-plane
-// -- the CPML memory psi_B of one slab axis arrive in shared memory by TMA
-// (cp.async.bulk.tensor) boxes covering the tile plus its halo, through a
-// ring of kStages buffers whose mbarriers complete on the transferred byte
-// count.  Thread 0 keeps the ring full and runs ahead into the next work
-// item, so the stream of planes has no gap between items.  Per plane:
-//   B phase  every thread forms B^{n+1/2} at its two points; warp 0 also forms
-//            the y0-1 row and half of warp 1 the x0-1 column of B that the E
-//            update needs from the neighbouring tiles; the plane of new B goes
-//            to one of two shared buffers, owned values to the new B array;
+// Work layout.  A CTA of 32 x 8 threads owns a 32 x 16 column tile -- each
+// thread an x-adjacent pair of points of one row -- and streams it along z
+// through a chunk of planes.  Each plane's E^n, B^{n-1/2} and -- where a CPML
+// slab reaches the tile-plane -- the CPML memory psi_B of one slab axis
+// arrive in shared memory by TMA (cp.async.bulk.tensor) boxes covering the
+// tile plus its halo, through a ring of kStages buffers whose mbarriers
+// complete on the transferred byte count.  Lane 0 of the last warp keeps the
+// ring full and runs ahead into the next work item, so the stream of planes
+// has no gap between items.  Per plane:
+//   B phase  every thread forms B^{n+1/2} at its pair; warp 0 also forms the
+//            y0-1 row and the x0-1 column of B that the E update needs from
+//            the neighbouring tiles; the plane of new B goes to one of two
+//            shared buffers, owned values to the new B array;
 //   barrier  (the only one per plane; it also frees the stage of the plane
-//            before, which thread 0 then refills);
-//   E phase  every thread forms Js^{n+1/2} and E^{n+1} at its two points from
-//            the shared B plane and the previous plane's B kept in registers.
-// E, B and psi_B ping-pong between two arrays (the other tiles only ever read
-// the old ones); Js and psi_E are owned by one thread and update in place.
-// Work items (tile, z chunk) come from an atomic counter, fetched one item
-// ahead; the grid fills every SM twice.  Periodic x / y seams, which a TMA box
-// cannot wrap, are patched from global memory after the box lands.
+//            before, which the producer then refills);
+//   E phase  every thread forms Js^{n+1/2} and E^{n+1} at its pair from the
+//            shared B plane and the previous plane's B kept in registers.
+// A pair lives in 64-bit registers and moves with 64-bit shared / global
+// accesses; its arithmetic uses the packed FP32x2 add / sub / mul / fma of
+// the sm_100 family.  E, B and psi_B ping-pong between two arrays (the other
+// tiles only ever read the old ones); Js and psi_E are owned by one thread
+// and update in place.  Work items (tile, z chunk) come from an atomic
+// counter through an order that hands out the slow items first; the grid
+// fills every SM twice.  Periodic x / y seams, which a TMA box cannot wrap,
+// are patched from global memory after the box lands.
 //
-// One code path serves every plane: x / y walls by per-column masks, the z
-// wall plane by plane masks, the CPML memory of the staged axis from shared
-// memory and of any further slab axis from global memory, and either one
-// precomputed {ca, cb, cj, 1/mu} record (all cells of the tile-plane alike)
-// or per-point coefficients set with the materials.  Sources, Mur planes and
-// per-face mu take branches that are uniform across the CTA.
+// x / y walls are per-point masks, the low z wall a plane mask; the CPML
+// memory of the staged axis comes from shared memory, that of any further
+// slab axis from global memory; a tile-plane whose cells are all alike uses
+// one precomputed {ca, cb, cj, 1/mu} record, the others per-point
+// coefficients set with the materials.  The plane body is compiled twice:
+// work items that meet a source, a Mur plane, a second CPML axis or varying
+// mu take the full body, all others a body without that code.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <math.h>
@@ -55,6 +60,7 @@ struct __align__(128) StageBuf {
 constexpr unsigned kEBytes = 3u * kEY * kEX * 4, kBBytes = 3u * kBY * kBX * 4, kPBBytes = 2u * kBY * kBX * 4;
 constexpr int kThreadsY = kTY / kRows;
 constexpr int kThreads = kTX * kThreadsY;
+constexpr int kProd = kTX * (kThreadsY - 1);   // the producer: lane 0 of the last warp (warp 0 forms the halo)
 constexpr size_t kBPlaneBytes = 3u * kBY * kBX * 4;
 
 // per-plane flags of a work item
@@ -359,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int PL = (int)P.plane;
     const bool mur = P.bc[2] == TF_BC_MUR;
 
-    auto fetch = [&]() -> int {   // thread 0: next work item or -1 (items that take the full loop come first)
+    auto fetch = [&]() -> int {   // producer: next work item or -1 (items that take the full loop come first)
         const long long d = (long long)(atomicAdd(O.ctr, 1ull) - O.base);
         return (d >= 0 && d < nitems) ? __ldg(O.order + d) : -1;
     };
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
     };
 
-    // ---------------------------------------------- producer (thread 0 only)
+    // ---------------------------------------------- producer (thread kProd only)
     // Items are numbered in the order this CTA takes them; item m lives in
     // slot m & 1, and the slot is refilled with item m + 2 once item m is done.
     // The producer may therefore run at most one item ahead of the consumer.
@@ -438,7 +444,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
     };
 
-    if (tid == 0) {
+    if (tid == kProd) {
         for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_item[0] = fetch();
@@ -452,14 +458,14 @@ __global__ void __launch_bounds__(kThreads, 2)
         rec_store(s_item[0], 0, r0);
         rec_store(s_item[1], 1, r1);
     }
-    if (tid == 0) pump();
+    if (tid == kProd) pump();
     __syncthreads();
 
     int cur = 0;
     bool aborted = false;
     unsigned long long seq0 = 0;   // ring sequence number of plane 0 of the current item
     unsigned it = 0;               // planes done by this CTA (selects the shared B plane)
-    int pend = -1;                 // thread 0: the item after the next one
+    int pend = -1;                 // producer: the item after the next one
     while (true) {
         const int item = s_item[cur];
         if (item < 0) break;
@@ -684,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (qq == 1) rec_store(s_item[cur ^ 1], cur ^ 1, rnext);   // loaded during plane 0
             // every thread is past the E phase of the plane before: its stage is free
             if (__syncthreads_or(!ok)) return false;
-            if (tid == 0) {
+            if (tid == kProd) {
                 consumed = g0;
                 pump();
                 if (qq == 0) pend = s_item[cur ^ 1] >= 0 ? fetch() : -1;
@@ -873,7 +879,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         seq0 += nq;
         // this item is done: its slot takes the item after the next one
         if (nq == 2) rec_store(s_item[cur ^ 1], cur ^ 1, rnext);   // a one-plane item: no plane 1
-        if (tid == 0) {
+        if (tid == kProd) {
             s_item[cur] = pend;
             ++c_ord;
         }
@@ -883,7 +889,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (aborted) {
         // a copy never landed: flag it, give the copies in flight a bounded
         // time to finish (they write this CTA's shared memory), stop
-        if (tid == 0) {
+        if (tid == kProd) {
             atomicOr(P.status, kStatusTimeout);
             for (unsigned long long gi = consumed; gi < issued; ++gi)
                 mbar_wait(&bar[gi % kStages], (unsigned)((gi / kStages) & 1));
