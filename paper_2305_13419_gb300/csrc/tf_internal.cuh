@@ -72,7 +72,7 @@ constexpr int kSX = kTX, kSY = kTY;          // tile stride
 constexpr int kEX = kTX + 8, kEY = kTY + 2;  // E box: x0-4 .. x0+35, y0-1 .. y0+kTY
 constexpr int kBX = kTX + 4, kBY = kTY + 1;  // B / psi_B box: x0-4 .. x0+31, y0-1 .. y0+kTY-1
 constexpr int kStages = 4;                   // planes in flight per CTA
-constexpr int kChunk = 16;                   // z planes per work item
+constexpr int kChunk = 8;                    // z planes per work item
 constexpr long long kSpinLimit = 1LL << 22;  // bounded mbarrier waits
 
 struct StepOut {
