@@ -9,5 +9,7 @@ Contents
   theory.py   -- closed forms of Sec. 4: complex wavenumber, skin depth,
                  reflection coefficient, cut-off; discrete dispersion
   qfit.py     -- Q-factor from a windowed probe DFT (exact finite-sum model)
+  esprit.py   -- damped-mode poles of a probe time series (ESPRIT), the
+                 estimator Sec. 5 names, as an independent Q check
   build.py    -- compiles the C stepper with gcc (no GPU needed)
 """
