@@ -52,6 +52,8 @@ def lib():
         L.or_probe_dft.argtypes = [vp, C.c_int, dp, dp]
         L.or_probe_series.argtypes = [vp, C.c_int, dp, C.c_int64]
         L.or_set_threads.argtypes = [C.c_int]
+        L.or_adjoint_dot_test.argtypes = [vp, C.c_int, C.c_uint64, dp, dp]
+        L.or_adjoint_run.argtypes = [vp, C.c_int64, C.c_int, ip, C.c_double, C.c_int64, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -191,6 +193,27 @@ class Grid:
         if rc:
             raise ValueError("series request beyond capacity")
         return out
+
+    def adjoint_dot_test(self, op: int, seed: int):
+        """(<M v, w>, <v, M^T w>) for Algorithm 1 sub-step `op` (1 B half step,
+        2 Js half step, 3 psi_E update, 4 theta step for E, 5 psi_B update)."""
+        l, r = C.c_double(), C.c_double()
+        if lib().or_adjoint_dot_test(self._h, int(op), int(seed), C.byref(l), C.byref(r)):
+            raise ValueError("or_adjoint_dot_test failed")
+        return l.value, r.value
+
+    def adjoint_run(self, nsteps: int, comp: int, p, freq: float, n0: int):
+        """J = |X(freq)|^2 of the probe DFT of E_comp at p over [n0, nsteps),
+        and dJ/d eps_r, dJ/d lambda_L per cell ([nz][ny][nx]), by the
+        discrete adjoint (runs the forward from level 0 first)."""
+        cs = (self.n[2], self.n[1], self.n[0])
+        ge, gl = np.zeros(cs), np.zeros(cs)
+        J = C.c_double()
+        p_ = (C.c_int * 3)(*[int(x) for x in p])
+        if lib().or_adjoint_run(self._h, int(nsteps), int(comp), p_, float(freq), int(n0), C.byref(J), _dp(ge),
+                                _dp(gl)):
+            raise ValueError("or_adjoint_run failed")
+        return J.value, ge, gl
 
     def fields(self):
         return [self.field(c) for c in range(9)]

@@ -610,3 +610,332 @@ int or_step(void* h, int64_t nsteps) {
     }
     return 0;
 }
+
+/* ===================================================================== */
+/* Discrete adjoint of Algorithm 1.                                       */
+/*                                                                        */
+/* With sources fixed, each sub-step of a step is a linear map of the     */
+/* state (E, B, Js, psi_E, psi_B).  Its transpose acts on the adjoint     */
+/* state; applying the transposes in reverse order, step by step from the */
+/* last, and adding the derivative of the objective at each sampled level */
+/* gives the adjoint trajectory.  The gradient of the objective with      */
+/* respect to a coefficient is the adjoint of the sub-step's output dotted */
+/* with the sub-step's derivative:                                        */
+/*   step 3 (theta scheme):  (eps + theta sigma dt) E' =                 */
+/*       (eps - (1 - theta) sigma dt) E + dt (curl H - Js)               */
+/*       => dE'/d eps_e = (E - E') / (eps_e + theta sigma_e dt);         */
+/*   steps 2 and 4:  Js' = Js + dt/2 kappa E  =>  dJs'/d kappa_e = dt/2 E. */
+/* Edge values are means of cell values (build_coefficients), so a cell's */
+/* gradient collects its edges' gradients with the same weights.          */
+/* All loops are serial: the transposed curls scatter into neighbours.    */
+/* ===================================================================== */
+
+typedef struct {
+    double *E[3], *B[3], *J[3], *psiB[3][3], *psiE[3][3];
+} adj_t;
+
+static void adj_alloc(const grid_t* g, adj_t* a) {
+    memset(a, 0, sizeof(*a));
+    for (int c = 0; c < 3; ++c) {
+        a->E[c] = dalloc(g->np); a->B[c] = dalloc(g->np); a->J[c] = dalloc(g->np);
+        for (int x = 0; x < 3; ++x) {
+            if (g->psiB[c][x]) a->psiB[c][x] = dalloc(g->np);
+            if (g->psiE[c][x]) a->psiE[c][x] = dalloc(g->np);
+        }
+    }
+}
+
+static void adj_free(adj_t* a) {
+    for (int c = 0; c < 3; ++c) {
+        free(a->E[c]); free(a->B[c]); free(a->J[c]);
+        for (int x = 0; x < 3; ++x) { free(a->psiB[c][x]); free(a->psiE[c][x]); }
+    }
+}
+
+/* transpose of half_step_B (B -= h curl E with the psi_B terms) */
+static void adj_half_step_B(const grid_t* g, adj_t* A) {
+    const double h = 0.5 * g->D.dt;
+    for (int cb = 0; cb < 3; ++cb)
+        for (int k = 0; k < g->N[2]; ++k)
+            for (int j = 0; j < g->N[1]; ++j)
+                for (int i = 0; i < g->N[0]; ++i) {
+                    long long q = IX(g, i, j, k);
+                    if (!g->updB[cb][q]) continue;
+                    int p[3] = {i, j, k};
+                    double v = -h * A->B[cb][q];
+                    for (int a = 0; a < 3; ++a) {
+                        if (a == cb) continue;
+                        int e = 3 - cb - a;
+                        double w = v * sgn(cb, a);
+                        int r[3] = {i, j, k};
+                        r[a] = nxt(g, a, p[a]);
+                        A->E[e][IX(g, r[0], r[1], r[2])] += w / g->D.d[a];
+                        A->E[e][q] -= w / g->D.d[a];
+                        if (A->psiB[cb][a]) A->psiB[cb][a][q] += w;
+                    }
+                }
+}
+
+/* transpose of advance_psiB (psi = b psi + c dE/da on updated faces) */
+static void adj_advance_psiB(const grid_t* g, adj_t* A) {
+    for (int cb = 0; cb < 3; ++cb)
+        for (int a = 0; a < 3; ++a) {
+            double* ps = A->psiB[cb][a];
+            if (!ps) continue;
+            int e = 3 - cb - a;
+            for (int k = 0; k < g->N[2]; ++k)
+                for (int j = 0; j < g->N[1]; ++j)
+                    for (int i = 0; i < g->N[0]; ++i) {
+                        long long q = IX(g, i, j, k);
+                        if (!g->updB[cb][q]) continue;
+                        int p[3] = {i, j, k};
+                        double w = ps[q], c = g->pcB[a][p[a]] / g->D.d[a];
+                        int r[3] = {i, j, k};
+                        r[a] = nxt(g, a, p[a]);
+                        A->E[e][IX(g, r[0], r[1], r[2])] += c * w;
+                        A->E[e][q] -= c * w;
+                        ps[q] = g->pbB[a][p[a]] * w;
+                    }
+        }
+}
+
+/* transpose of half_step_Js; with gk != NULL also dJ/dkappa_e += dt/2 Js_adj E */
+static void adj_half_step_Js(const grid_t* g, adj_t* A, double* const gk[3], double* const Ef[3]) {
+    const double h = 0.5 * g->D.dt;
+    for (int c = 0; c < 3; ++c)
+        for (long long q = 0; q < g->np; ++q) {
+            if (!g->updJ[c][q]) continue;
+            A->E[c][q] += h * g->kapE[c][q] * A->J[c][q];
+            if (gk) gk[c][q] += h * A->J[c][q] * Ef[c][q];
+        }
+}
+
+/* transpose of full_step_E; with ge != NULL also dJ/deps_r,e (eps_e = EPS0 eps_r,e)
+   += E_adj' EPS0 (E - E') / (eps_e + theta sigma_e dt), E = Eb, E' = Ea */
+static void adj_full_step_E(const grid_t* g, adj_t* A, double* const ge[3], double* const Eb[3],
+                            double* const Ea[3]) {
+    const double dt = g->D.dt, th = g->D.theta;
+    for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < g->N[2]; ++k)
+            for (int j = 0; j < g->N[1]; ++j)
+                for (int i = 0; i < g->N[0]; ++i) {
+                    long long q = IX(g, i, j, k);
+                    if (!g->updE[c][q]) continue;
+                    int p[3] = {i, j, k};
+                    double eps = g->epsE[c][q], s = g->sigE[c][q] * dt / eps;
+                    if (ge) ge[c][q] += A->E[c][q] * EPS0 * (Eb[c][q] - Ea[c][q]) / (eps + th * g->sigE[c][q] * dt);
+                    double e = A->E[c][q] / (1.0 + th * s);
+                    A->E[c][q] = (1.0 - (1.0 - th) * s) * e;
+                    double v = dt / eps * e;
+                    A->J[c][q] -= v;
+                    for (int a = 0; a < 3; ++a) {
+                        if (a == c) continue;
+                        int hc = 3 - c - a;
+                        double w = v * sgn(c, a);
+                        int r[3] = {i, j, k};
+                        r[a] = prv(g, a, p[a]);
+                        long long qr = IX(g, r[0], r[1], r[2]);
+                        A->B[hc][q] += w / (g->muF[hc][q] * g->D.d[a]);
+                        A->B[hc][qr] -= w / (g->muF[hc][qr] * g->D.d[a]);
+                        if (A->psiE[c][a]) A->psiE[c][a][q] += w;
+                    }
+                }
+}
+
+/* transpose of advance_psiE (psi = b psi + c dH/da on updated edges) */
+static void adj_advance_psiE(const grid_t* g, adj_t* A) {
+    for (int c = 0; c < 3; ++c)
+        for (int a = 0; a < 3; ++a) {
+            double* ps = A->psiE[c][a];
+            if (!ps) continue;
+            int hc = 3 - c - a;
+            for (int k = 0; k < g->N[2]; ++k)
+                for (int j = 0; j < g->N[1]; ++j)
+                    for (int i = 0; i < g->N[0]; ++i) {
+                        long long q = IX(g, i, j, k);
+                        if (!g->updE[c][q]) continue;
+                        int p[3] = {i, j, k};
+                        double w = ps[q], cc = g->pcE[a][p[a]] / g->D.d[a];
+                        int r[3] = {i, j, k};
+                        r[a] = prv(g, a, p[a]);
+                        long long qr = IX(g, r[0], r[1], r[2]);
+                        A->B[hc][q] += cc * w / g->muF[hc][q];
+                        A->B[hc][qr] -= cc * w / g->muF[hc][qr];
+                        ps[q] = g->pbE[a][p[a]] * w;
+                    }
+        }
+}
+
+/* ------------------------------------------------------ dot-product test */
+static uint64_t sm64(uint64_t* s) {   /* SplitMix64 */
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+static double urand(uint64_t* s) { return (double)(sm64(s) >> 11) * (1.0 / 9007199254740992.0) - 0.5; }
+
+/* all state arrays of g (fwd) or A (adjoint) in a fixed order */
+static int state_arrays(grid_t* g, adj_t* A, double** out) {
+    int n = 0;
+    for (int c = 0; c < 3; ++c) out[n++] = A ? A->E[c] : g->E[c];
+    for (int c = 0; c < 3; ++c) out[n++] = A ? A->B[c] : g->B[c];
+    for (int c = 0; c < 3; ++c) out[n++] = A ? A->J[c] : g->J[c];
+    for (int c = 0; c < 3; ++c)
+        for (int a = 0; a < 3; ++a) {
+            if (g->psiB[c][a]) out[n++] = A ? A->psiB[c][a] : g->psiB[c][a];
+            if (g->psiE[c][a]) out[n++] = A ? A->psiE[c][a] : g->psiE[c][a];
+        }
+    return n;
+}
+
+/* <M v, w> and <v, M^T w> for sub-step `op` (1: B half step, 2: Js half
+   step, 3: psi_E update, 4: E theta step, 5: psi_B update) with random v, w.
+   Overwrites the forward state. */
+int or_adjoint_dot_test(void* h, int op, uint64_t seed, double* lhs, double* rhs) {
+    grid_t* g = (grid_t*)h;
+    if (op < 1 || op > 5 || !lhs || !rhs) return 1;
+    adj_t A;
+    adj_alloc(g, &A);
+    double *fs[40], *as[40];
+    const int n = state_arrays(g, NULL, fs);
+    state_arrays(g, &A, as);
+    double** v = (double**)calloc((size_t)n, sizeof(double*));
+    uint64_t s = seed;
+    for (int m = 0; m < n; ++m) {
+        v[m] = dalloc(g->np);
+        for (long long q = 0; q < g->np; ++q) fs[m][q] = v[m][q] = urand(&s);
+        for (long long q = 0; q < g->np; ++q) as[m][q] = urand(&s);
+    }
+    double** w = (double**)calloc((size_t)n, sizeof(double*));
+    for (int m = 0; m < n; ++m) {
+        w[m] = dalloc(g->np);
+        memcpy(w[m], as[m], sizeof(double) * (size_t)g->np);
+    }
+    switch (op) {
+        case 1: half_step_B(g); adj_half_step_B(g, &A); break;
+        case 2: half_step_Js(g); adj_half_step_Js(g, &A, NULL, NULL); break;
+        case 3: advance_psiE(g); adj_advance_psiE(g, &A); break;
+        case 4: full_step_E(g); adj_full_step_E(g, &A, NULL, NULL, NULL); break;
+        default: advance_psiB(g); adj_advance_psiB(g, &A); break;
+    }
+    long double l = 0, r = 0;
+    for (int m = 0; m < n; ++m)
+        for (long long q = 0; q < g->np; ++q) {
+            l += (long double)fs[m][q] * w[m][q];
+            r += (long double)v[m][q] * as[m][q];
+        }
+    *lhs = (double)l;
+    *rhs = (double)r;
+    for (int m = 0; m < n; ++m) { free(v[m]); free(w[m]); }
+    free(v);
+    free(w);
+    adj_free(&A);
+    return 0;
+}
+
+/* ------------------------------------------------------ adjoint gradient */
+/* Objective J = |X|^2, X = dt sum_{n=n0}^{N-1} E_comp(p)^n exp(-i 2 pi f n dt)
+   (the probe DFT at one frequency).  Runs nsteps of Algorithm 1 from the
+   handle's current state (level 0; no Mur walls), then the adjoint back to
+   level 0, and returns J and dJ/d eps_r and dJ/d lambda_L per cell (0 for
+   cells that are not superconducting).  The handle is left at level nsteps. */
+int or_adjoint_run(void* h, int64_t nsteps, int comp, const int pr[3], double freq, int64_t n0, double* Jout,
+                   double* g_eps, double* g_lam) {
+    grid_t* g = (grid_t*)h;
+    if (g->level != 0 || g->D.bc[2] == OR_BC_MUR || nsteps < 1 || comp < 0 || comp > 2) return 1;
+    for (int a = 0; a < 3; ++a)
+        if (pr[a] < 0 || pr[a] >= g->N[a]) return 1;
+    const long long np = g->np, qp = IX(g, pr[0], pr[1], pr[2]);
+    const double dt = g->D.dt;
+    /* forward, keeping E^n (n = 0..N) and the theta-step output before sources */
+    double* Eh = dalloc(3 * np * (nsteps + 1));
+    double* Ep = dalloc(3 * np * nsteps);
+    if (!Eh || !Ep) { free(Eh); free(Ep); return 2; }
+#define EH(n, c) (Eh + ((long long)(n) * 3 + (c)) * np)
+#define EP(n, c) (Ep + ((long long)(n) * 3 + (c)) * np)
+    long double xr = 0, xi = 0;
+    if (!g->psi_ready) { advance_psiB(g); g->psi_ready = 1; }
+    for (int64_t s = 0; s < nsteps; ++s) {
+        for (int c = 0; c < 3; ++c) memcpy(EH(s, c), g->E[c], sizeof(double) * (size_t)np);
+        if (g->level >= n0) {
+            long double ph = (long double)freq * (long double)dt * (long double)g->level;
+            ph -= floorl(ph);
+            xr += g->E[comp][qp] * cosl(TWO_PI_L * ph) * dt;
+            xi -= g->E[comp][qp] * sinl(TWO_PI_L * ph) * dt;
+        }
+        sample_probes(g);
+        half_step_B(g);
+        half_step_Js(g);
+        advance_psiE(g);
+        full_step_E(g);
+        for (int c = 0; c < 3; ++c) memcpy(EP(s, c), g->E[c], sizeof(double) * (size_t)np);
+        apply_sources(g, (double)(g->level + 1) * dt);
+        half_step_Js(g);
+        advance_psiB(g);
+        half_step_B(g);
+        g->level++;
+    }
+    for (int c = 0; c < 3; ++c) memcpy(EH(nsteps, c), g->E[c], sizeof(double) * (size_t)np);
+    *Jout = (double)(xr * xr + xi * xi);
+    /* adjoint sweep */
+    adj_t A;
+    adj_alloc(g, &A);
+    double *ge[3], *gk[3];
+    for (int c = 0; c < 3; ++c) { ge[c] = dalloc(np); gk[c] = dalloc(np); }
+    for (int64_t s = nsteps - 1; s >= 0; --s) {
+        double *Eb[3], *Ea[3], *En[3];
+        for (int c = 0; c < 3; ++c) { Eb[c] = EH(s, c); Ea[c] = EP(s, c); En[c] = EH(s + 1, c); }
+        adj_half_step_B(g, &A);                /* 5 */
+        adj_advance_psiB(g, &A);
+        adj_half_step_Js(g, &A, gk, En);       /* 4 */
+        adj_full_step_E(g, &A, ge, Eb, Ea);    /* 3 */
+        adj_advance_psiE(g, &A);
+        adj_half_step_Js(g, &A, gk, Eb);       /* 2 */
+        adj_half_step_B(g, &A);                /* 1 */
+        if (s >= n0) {                          /* dJ/dE^n at the probe: 2 dt Re(conj(X) w^n) */
+            long double ph = (long double)freq * (long double)dt * (long double)s;
+            ph -= floorl(ph);
+            A.E[comp][qp] += 2.0 * dt * (double)(xr * cosl(TWO_PI_L * ph) - xi * sinl(TWO_PI_L * ph));
+        }
+    }
+    /* edges -> cells with the weights of build_coefficients */
+    memset(g_eps, 0, sizeof(double) * (size_t)g->nc);
+    memset(g_lam, 0, sizeof(double) * (size_t)g->nc);
+    for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < g->N[2]; ++k)
+            for (int j = 0; j < g->N[1]; ++j)
+                for (int i = 0; i < g->N[0]; ++i) {
+                    long long q = IX(g, i, j, k);
+                    if (!g->updE[c][q]) continue;
+                    int p[3] = {i, j, k};
+                    int b1 = (c + 1) % 3, b2 = (c + 2) % 3, nk = 0;
+                    long long cells[4];
+                    for (int u = 0; u < 2; ++u)
+                        for (int v = 0; v < 2; ++v) {
+                            int cc[3];
+                            cc[c] = p[c];
+                            cc[b1] = wrapc(g, b1, p[b1] - u);
+                            cc[b2] = wrapc(g, b2, p[b2] - v);
+                            cells[2 * u + v] = CI(g, cc[0], cc[1], cc[2]);
+                            nk += g->kap_c[cells[2 * u + v]] > 0.0;
+                        }
+                    for (int m = 0; m < 4; ++m) {
+                        long long cm = cells[m];
+                        g_eps[cm] += 0.25 * ge[c][q];
+                        double kc = g->kap_c[cm];
+                        if (kc > 0.0) {
+                            double wgt = g->D.edge_rule == 1 ? 0.25 : 1.0 / nk;
+                            double lam = 1.0 / sqrt(kc * MU0 * g->mu_c[cm]);
+                            g_lam[cm] += gk[c][q] * wgt * (-2.0 * kc / lam);
+                        }
+                    }
+                }
+#undef EH
+#undef EP
+    for (int c = 0; c < 3; ++c) { free(ge[c]); free(gk[c]); }
+    adj_free(&A);
+    free(Eh);
+    free(Ep);
+    return 0;
+}

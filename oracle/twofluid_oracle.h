@@ -74,6 +74,18 @@ int    or_probe_series(void* h, int id, double* out, int64_t n);
 int    or_get_coeff(void* h, int kind, int comp, double* dst);
 int    or_set_threads(int n);
 
+/* Discrete adjoint of Algorithm 1 (test infrastructure, serial).
+   or_adjoint_dot_test: <M v, w> and <v, M^T w> for one sub-step with random
+   v, w (op 1 B half step, 2 Js half step, 3 psi_E update, 4 theta step for E,
+   5 psi_B update); overwrites the state.
+   or_adjoint_run: J = |X|^2 of the one-frequency probe DFT
+   X = dt sum_{n0 <= n < nsteps} E_comp(p)^n exp(-i 2 pi f n dt), and dJ/d eps_r
+   and dJ/d lambda_L per cell ([nz][ny][nx]), over nsteps from level 0
+   (periodic, PEC or CPML walls; not Mur).  Leaves the handle at level nsteps. */
+int    or_adjoint_dot_test(void* h, int op, uint64_t seed, double* lhs, double* rhs);
+int    or_adjoint_run(void* h, int64_t nsteps, int comp, const int p[3], double freq, int64_t n0,
+                      double* J, double* g_eps, double* g_lam);
+
 #ifdef __cplusplus
 }
 #endif
