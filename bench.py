@@ -347,16 +347,53 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(w, budget_s=args.cpu_budget)
 
+    adj = None
+    if rank == 0 and not args.no_adjoint:
+        g.close()
+        del g
+        adj = run_adjoint(args)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_block(state_bytes), "roofline": roof, "cpu_baseline": base, "e2e": e2e,
-                "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary()}
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "adjoint": adj}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_adjoint(args):
+    """Gradient of |X(f0)|^2 with respect to every cell's eps_r and lambda_L
+    on the 256 x 128 x 64 adjoint CPW by the discrete adjoint (forward with
+    checkpoints every 256 steps, per-segment recompute, transposed steps),
+    timed whole, against the plain step on the same grid."""
+    import time
+    import torch
+    from paper_2305_13419_gb300 import twofluid as tf
+    from paper_2305_13419_gb300 import workloads as W
+    w = W.cpw_adjoint(nsteps=args.adjoint_steps)
+    g = tf.Grid.from_workload(w)
+    g.step(20)
+    kt = g.step_timed(200)
+    g.sync()
+    plain = sum(v[0] for v in kt.values())
+    g.close()
+    del g
+    g = tf.Grid.from_workload(w)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, ge, gl = g.adjoint(args.adjoint_steps, 0, 0, segment=256)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    per = ms / args.adjoint_steps
+    return {"workload": w.name, "steps": args.adjoint_steps, "segment": 256, "ms": ms, "ms_per_step": per,
+            "plain_ms_per_step": plain, "vs_plain_step": per / plain,
+            "gcell_updates_per_s": w.ncells * args.adjoint_steps / (ms * 1e-3) / 1e9,
+            "objective": J, "grad_eps_absmax": float(ge.abs().max()), "grad_lambda_absmax": float(gl.abs().max()),
+            "includes": "forward with checkpoints, per-segment recompute, adjoint steps, gradient reduction"}
 
 
 def run_e2e(args, w, dev):
@@ -406,6 +443,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=8000)
     args = ap.parse_args(argv)
     ws, rank, local = dist_env()
     if args.warmup < 3:

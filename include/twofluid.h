@@ -204,6 +204,30 @@ tf_status tf_checkpoint_size(tf_handle h, size_t* bytes);
 tf_status tf_checkpoint_save(tf_handle h, void* dst, size_t bytes, int on_device);
 tf_status tf_checkpoint_load(tf_handle h, const void* src, size_t bytes, int on_device);
 
+/* Discrete adjoint of the time stepping (Algorithm 1, Sec. 3): the gradient
+ * of the objective J = |X_k|^2 -- X_k the FP64 DFT of probe `probe` at its
+ * frequency index k over its window [n0, nsteps) -- with respect to the
+ * relative permittivity and the London depth of every cell.
+ *   The handle must hold the state at rest before its first step (level 0,
+ *   not yet stepped; fields as set, normally zero) with materials, sources
+ *   and probes configured; no Mur walls (TF_ENOTSUP).  The call runs nsteps
+ *   forward, saving a checkpoint every `segment` steps into the scratch,
+ *   then walks the segments backwards: each is recomputed from its
+ *   checkpoint with E kept at every level, and the transposed step runs back
+ *   through it, summing per-edge gradients in FP64.
+ *   scratch   caller-owned device memory of at least tf_adjoint_scratch_size
+ *             bytes (checkpoints, one segment of E history, the adjoint
+ *             state, the gradient sums); TF_ENOMEM if smaller;
+ *   J         host double: the objective;
+ *   grad_eps, grad_lambda  device float arrays [nz][ny][nx] (cells):
+ *             dJ/d eps_r and dJ/d lambda_L (per metre), the latter 0 on
+ *             cells that are not superconducting.
+ * On return the handle holds the state after nsteps (as tf_step would).
+ * Synchronises the stream. */
+tf_status tf_adjoint_scratch_size(tf_handle h, int64_t nsteps, int segment, size_t* bytes);
+tf_status tf_adjoint_run(tf_handle h, int64_t nsteps, int probe, int freq_index, int segment, void* scratch,
+                         size_t bytes, double* J, float* grad_eps, float* grad_lambda);
+
 /* Q-factor of one damped mode from probe id's DFT (Sec. 5 reports Q and the
  * resonance from the ring-down): fits X_k = dt sum_{n0<=n<N} (a z^n + c.c.)
  * w_k^n, z = exp((-alpha + i omega0) dt), in FP64 on the GPU.  f_guess and

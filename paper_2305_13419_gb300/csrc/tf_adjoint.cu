@@ -1,0 +1,228 @@
+// tf_adjoint.cu -- discrete adjoint of the fused step (sm_103a).
+//
+// With sources fixed, one fused step of Algorithm 1 (arXiv 2305.13419,
+// Sec. 3) is a linear map of the state (E, Bt, Jt, psi_B, psi_E):
+//   psi_B' = bB psi_B + cB dE              (CPML slabs, updated faces)
+//   Bt'    = Bt - curl_r E - sB psi_B'      (sB(c, a) = -curl_sign(c, a))
+//   Jt'    = Jt + cj E
+//   psi_E' = bE psi_E + cE dH(Bt'/mu)      (CPML slabs, updated edges)
+//   E'     = ca E + cb (curl_r (Bt'/mu) + sE psi_E' - Jt')   (sE = curl_sign)
+// (curl_r: the Yee curls with the r_a = c0 dt / d_a weights; ca, cb, cj the
+// per-edge coefficients, 1, 0, 0 on edges the step leaves alone).  Its
+// transpose, applied to the adjoint state (Eh, Bh, Jh, psi_Bh, psi_Eh), is
+//   e          = cb Eh'
+//   psi_Eh'tot = psi_Eh' + sE e
+//   Bh'tot     = Bh' + (1/mu) [transposed backward differences of
+//                sE r e + cE psi_Eh'tot]                     (face pass)
+//   psi_Bh'tot = bB-scaled psi_Bh' + sB Bh'tot
+//   Jh         = Jh' - e
+//   psi_Eh     = bE psi_Eh'tot
+//   Eh         = ca Eh' + cj Jh + [transposed forward differences of
+//                -curl_sign r Bh'tot + cB psi_Bh'tot]         (edge pass)
+// and the gradient of the objective collects, per edge,
+//   dJ/d eps_e += Eh' cb (E^n - E'_no-source)     (Alg. 1 step 3, theta scheme)
+//   dJ/d kt_e  += Jh E^n                           (steps 4 + 2)
+// The face pass writes Bh'tot and psi_Bh'tot in place (the bB factor of the
+// next step is applied when psi_Bh is next read); the edge pass reads its own
+// edge and the faces around it, so both update in place.  One thread per
+// storage point handles its three components.
+#include <math.h>
+
+#include "tf_internal.cuh"
+
+namespace tf {
+
+namespace {
+
+constexpr int kAdjThreads = 256;
+
+__device__ __forceinline__ void point_of(const Params& P, long long t, int p[3]) {
+    const long long xy = (long long)P.pitch * P.N[1];
+    p[2] = (int)(t / xy);
+    const long long r = t - (long long)p[2] * xy;
+    p[1] = (int)(r / P.pitch);
+    p[0] = (int)(r - (long long)p[1] * P.pitch);
+}
+
+// weight on dH_a(H_h)(x) of edge e at x (h = 3 - e - a), zero for edges the step leaves alone
+__device__ __forceinline__ float edge_weight(const Params& P, const AdjState& A, int e, int a, const int x[3]) {
+    const long long q = lin(P, x[0], x[1], x[2]);
+    const float cb = __ldg(P.cb[e] + q);
+    if (cb == 0.f) return 0.f;
+    const float s = curl_sign(e, a);
+    const float ev = cb * A.E[e][q];
+    float w = s * P.r[a] * ev;
+    if (A.psiE[e][a] && in_slab(P, a, x[a])) w += __ldg(P.pcE[a] + x[a]) * (A.psiE[e][a][q] + s * ev);
+    return w;
+}
+
+// weight on dE_a(E_e)(y) of face c at y (e = 3 - c - a), zero for faces the step leaves alone
+__device__ __forceinline__ float face_weight(const Params& P, const AdjState& A, int c, int a, const int y[3]) {
+    if (!upd_B(P, c, y)) return 0.f;
+    const long long q = lin(P, y[0], y[1], y[2]);
+    float u = -curl_sign(c, a) * P.r[a] * A.B[c][q];
+    if (A.psiB[c][a] && in_slab(P, a, y[a])) u += __ldg(P.pcB[a] + y[a]) * A.psiB[c][a][q];
+    return u;
+}
+
+}  // namespace
+
+// face pass: Bh'tot = Bh' + (1/mu) sum_a [w(y) - w(y + a)], psi_Bh'tot
+__global__ void __launch_bounds__(kAdjThreads) k_adj_faces(Params P, AdjState A) {
+    const long long t = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
+    if (t >= (long long)P.plane * P.N[2]) return;
+    int p[3];
+    point_of(P, t, p);
+    if (p[0] >= P.N[0]) return;
+    const long long q = lin(P, p[0], p[1], p[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (!upd_B(P, c, p)) continue;
+        float hsum = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a == c) continue;
+            const int e = 3 - c - a;
+            int x[3] = {p[0], p[1], p[2]};
+            x[a] = nxt(P, a, p[a]);
+            hsum += edge_weight(P, A, e, a, p) - edge_weight(P, A, e, a, x);
+        }
+        const float bt = A.B[c][q] + hsum * inv_mu_face(P, c, p);
+        A.B[c][q] = bt;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a == c || !A.psiB[c][a] || !in_slab(P, a, p[a])) continue;
+            A.psiB[c][a][q] = __ldg(P.pbB[a] + p[a]) * A.psiB[c][a][q] - curl_sign(c, a) * bt;
+        }
+    }
+}
+
+// edge pass: Jh, psi_Eh, Eh; per-edge gradients; the objective's derivative at the probe
+__global__ void __launch_bounds__(kAdjThreads) k_adj_edges(Params P, AdjState A, Sources S, AdjStep st) {
+    const long long t = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
+    if (t >= (long long)P.plane * P.N[2]) return;
+    int p[3];
+    point_of(P, t, p);
+    if (p[0] >= P.N[0]) return;
+    const long long q = lin(P, p[0], p[1], p[2]);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const float ep = A.E[e][q];
+        // transposed forward differences of the face weights
+        float d = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a == e) continue;
+            const int c = 3 - e - a;
+            if (P.per[a] || p[a] > 0) {
+                int y[3] = {p[0], p[1], p[2]};
+                y[a] = prv(P, a, p[a]);
+                d += face_weight(P, A, c, a, y);
+            }
+            d -= face_weight(P, A, c, a, p);
+        }
+        const float cb = __ldg(P.cb[e] + q);
+        float enew = ep + d;
+        if (cb != 0.f) {
+            const float ev = cb * ep, cj = __ldg(P.cj[e] + q);
+            const float jh = A.J[e][q] - ev;
+            A.J[e][q] = jh;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a == e || !A.psiE[e][a] || !in_slab(P, a, p[a])) continue;
+                A.psiE[e][a][q] = __ldg(P.pbE[a] + p[a]) * (A.psiE[e][a][q] + curl_sign(e, a) * ev);
+            }
+            enew = __ldg(P.ca[e] + q) * ep + cj * jh + d;
+            // gradients: E^n, and E^{n+1} without this step's soft sources
+            const float en = st.En[e][q];
+            float e1 = st.En1[e][q];
+            for (int s = 0; s < S.n; ++s)
+                if (S.comp[s] == e && p[0] >= S.lo[s][0] && p[0] < S.hi[s][0] && p[1] >= S.lo[s][1] &&
+                    p[1] < S.hi[s][1] && p[2] >= S.lo[s][2] && p[2] < S.hi[s][2])
+                    e1 -= S.amp[s];
+            A.gE[e][q] += (double)ep * (double)cb * (double)(en - e1);
+            if (cj > 0.f) A.gK[e][q] += (double)jh * (double)en;
+        }
+        if (e == st.probe_comp && q == st.probe_q) enew += st.probe_src;
+        A.E[e][q] = enew;
+    }
+}
+
+// per cell: dJ/d eps_r and dJ/d lambda_L from the per-edge sums, with the
+// weights of the edge rule (eps: mean of 4 cells; kt: mean over the 4 cells
+// or over the superconducting ones)
+__global__ void __launch_bounds__(kAdjThreads) k_adj_cells(Params P, AdjState A, float dt_c0, float* g_eps,
+                                                          float* g_lam) {
+    const long long t = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
+    const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
+    if (t >= nc) return;
+    const int cell[3] = {(int)(t % P.n[0]), (int)((t / P.n[0]) % P.n[1]), (int)(t / ((long long)P.n[0] * P.n[1]))};
+    const long long m = lin(P, cell[0], cell[1], cell[2]);
+    const float kc = __ldg(P.kap + m);
+    double ge = 0.0, gk = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int b1 = (c + 1) % 3, b2 = (c + 2) % 3;
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                // edge E_c whose cell (p[c], p[b1] - u, p[b2] - v) is this cell
+                int x[3];
+                x[c] = cell[c];
+                x[b1] = cell[b1] + u;
+                x[b2] = cell[b2] + v;
+                if (x[b1] >= P.N[b1]) { if (!P.per[b1]) continue; x[b1] -= P.N[b1]; }
+                if (x[b2] >= P.N[b2]) { if (!P.per[b2]) continue; x[b2] -= P.N[b2]; }
+                if (!upd_E(P, c, x)) continue;
+                const long long q = lin(P, x[0], x[1], x[2]);
+                ge += 0.25 * A.gE[c][q];
+                if (kc > 0.f) {
+                    float wgt = 0.25f;
+                    if (P.edge_rule != TF_EDGE_PLAIN_MEAN) {
+                        int nk = 0;
+#pragma unroll
+                        for (int uu = 0; uu < 2; ++uu)
+#pragma unroll
+                            for (int vv = 0; vv < 2; ++vv) {
+                                int cc[3];
+                                cc[c] = x[c];
+                                cc[b1] = uu ? prv(P, b1, x[b1]) : x[b1];
+                                cc[b2] = vv ? prv(P, b2, x[b2]) : x[b2];
+                                nk += __ldg(P.kap + lin(P, cc[0], cc[1], cc[2])) > 0.f;
+                            }
+                        wgt = nk ? 1.f / (float)nk : 0.f;
+                    }
+                    gk += (double)wgt * A.gK[c][q];
+                }
+            }
+    }
+    g_eps[t] = (float)ge;
+    float gl = 0.f;
+    if (kc > 0.f) {   // kt = (c0 dt / lambda)^2 / mu_r: d kt / d lambda = -2 kt / lambda
+        const float lam = dt_c0 / sqrtf(kc * __ldg(P.mu + m));
+        gl = (float)(gk * (-2.0 * (double)kc / (double)lam));
+    }
+    g_lam[t] = gl;
+}
+
+static unsigned adj_blocks(const Params& P) {
+    return (unsigned)(((long long)P.plane * P.N[2] + kAdjThreads - 1) / kAdjThreads);
+}
+
+cudaError_t launch_adjoint_step(const Params& P, const AdjState& A, const Sources& S, const AdjStep& st,
+                                cudaStream_t stream) {
+    k_adj_faces<<<adj_blocks(P), kAdjThreads, 0, stream>>>(P, A);
+    k_adj_edges<<<adj_blocks(P), kAdjThreads, 0, stream>>>(P, A, S, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0, float* g_eps, float* g_lam,
+                                 cudaStream_t stream) {
+    const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
+    k_adj_cells<<<(unsigned)((nc + kAdjThreads - 1) / kAdjThreads), kAdjThreads, 0, stream>>>(P, A, dt_c0, g_eps,
+                                                                                              g_lam);
+    return cudaGetLastError();
+}
+
+}  // namespace tf

@@ -777,6 +777,133 @@ tf_status tf_checkpoint_load(tf_handle h, const void* src, size_t bytes, int on_
     return TF_OK;
 }
 
+// ---------------------------------------------------------------- adjoint
+namespace {
+
+struct AdjLayout {
+    size_t ck, nck, off_ck, off_hist, off_state, off_grad, bytes;
+    int64_t nseg;
+};
+
+AdjLayout adj_layout(const tf_ctx* h, int64_t nsteps, int segment) {
+    AdjLayout A{};
+    const size_t fb = align_up(sizeof(float) * (size_t)h->L.total);
+    A.nseg = (nsteps + segment - 1) / segment;
+    A.ck = align_up(ckpt_bytes(h));
+    A.nck = (size_t)A.nseg + 1;
+    size_t o = 0;
+    A.off_ck = o;    o += A.nck * A.ck;
+    A.off_hist = o;  o += (size_t)(segment + 1) * 3 * fb;
+    A.off_state = o; o += (size_t)(9 + 4 * h->L.ncpml_axes) * fb;
+    A.off_grad = o;  o += 6 * align_up(sizeof(double) * (size_t)h->L.total);
+    A.bytes = o;
+    return A;
+}
+
+}  // namespace
+
+tf_status tf_adjoint_scratch_size(tf_handle h, int64_t nsteps, int segment, size_t* bytes) {
+    if (!h || !bytes || nsteps < 1 || segment < 1) return TF_EINVAL;
+    *bytes = adj_layout(h, nsteps, segment).bytes;
+    return TF_OK;
+}
+
+tf_status tf_adjoint_run(tf_handle h, int64_t nsteps, int probe, int freq_index, int segment, void* scratch,
+                         size_t bytes, double* J, float* grad_eps, float* grad_lambda) {
+    if (!h || nsteps < 1 || segment < 1 || !scratch || !J || !grad_eps || !grad_lambda) return TF_EINVAL;
+    if (probe < 0 || probe >= h->R.n || freq_index < 0 || freq_index >= h->R.nfreq[probe]) return TF_EINVAL;
+    if (h->level != 0 || h->primed) return TF_ESTATE;
+    if (h->desc.bc[2].kind == TF_BC_MUR) return TF_ENOTSUP;
+    const AdjLayout A = adj_layout(h, nsteps, segment);
+    if (bytes < A.bytes) return TF_ENOMEM;
+    char* sc = (char*)scratch;
+    const size_t fb = align_up(sizeof(float) * (size_t)h->L.total);
+    const size_t gb = align_up(sizeof(double) * (size_t)h->L.total);
+    tf_status rc;
+    // forward run, a checkpoint at the start of every segment and at the end
+    for (int64_t s = 0; s < A.nseg; ++s) {
+        if ((rc = tf_checkpoint_save(h, sc + A.off_ck + s * A.ck, A.ck, 1)) != TF_OK) return rc;
+        const int64_t len = (s + 1) * segment <= nsteps ? segment : nsteps - s * segment;
+        if ((rc = tf_step(h, len)) != TF_OK) return rc;
+    }
+    if ((rc = tf_checkpoint_save(h, sc + A.off_ck + A.nseg * A.ck, A.ck, 1)) != TF_OK) return rc;
+    if ((rc = tf_sync(h)) != TF_OK) return rc;
+    // objective J = |X|^2 from the probe's FP64 DFT
+    double re[TF_MAX_FREQS], im[TF_MAX_FREQS];
+    if ((rc = tf_read_probe_dft(h, probe, re, im)) != TF_OK) return rc;
+    const double xr = re[freq_index], xi = im[freq_index];
+    *J = xr * xr + xi * xi;
+    const double f = h->freqs[probe][freq_index];
+    // adjoint state and gradient sums start at zero
+    TF_CUDA(cudaMemsetAsync(sc + A.off_state, 0, A.bytes - A.off_state, h->stream));
+    AdjState S{};
+    {
+        int m = 0;
+        auto fa = [&]() { return (float*)(sc + A.off_state + (size_t)(m++) * fb); };
+        for (int c = 0; c < 3; ++c) S.E[c] = fa();
+        for (int c = 0; c < 3; ++c) S.B[c] = fa();
+        for (int c = 0; c < 3; ++c) S.J[c] = fa();
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) {
+                S.psiB[c][a] = nullptr;
+                S.psiE[c][a] = nullptr;
+            }
+        for (int a = 0; a < 3; ++a) {
+            if (h->desc.bc[a].kind != TF_BC_CPML) continue;
+            for (int c = 0; c < 3; ++c) {
+                if (c == a) continue;
+                S.psiB[c][a] = fa();
+                S.psiE[c][a] = fa();
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            S.gE[c] = (double*)(sc + A.off_grad + (size_t)c * gb);
+            S.gK[c] = (double*)(sc + A.off_grad + (size_t)(3 + c) * gb);
+        }
+    }
+    Sources src;
+    fill_sources(h, src);
+    const int64_t n0 = h->R.n0[probe];
+    auto hist = [&](int64_t m, int c) { return (float*)(sc + A.off_hist + ((size_t)m * 3 + c) * fb); };
+    for (int64_t s = A.nseg - 1; s >= 0; --s) {
+        // recompute the segment, keeping E at every level
+        if ((rc = tf_checkpoint_load(h, sc + A.off_ck + s * A.ck, A.ck, 1)) != TF_OK) return rc;
+        const int64_t len = (s + 1) * segment <= nsteps ? segment : nsteps - s * segment;
+        for (int64_t m = 0; m <= len; ++m) {
+            for (int c = 0; c < 3; ++c)
+                TF_CUDA(cudaMemcpyAsync(hist(m, c), h->P.E[c], sizeof(float) * (size_t)h->L.total,
+                                        cudaMemcpyDeviceToDevice, h->stream));
+            if (m < len && (rc = tf_step(h, 1)) != TF_OK) return rc;
+        }
+        // adjoint steps back through the segment
+        for (int64_t m = len - 1; m >= 0; --m) {
+            const int64_t n = s * segment + m;
+            AdjStep st;
+            for (int c = 0; c < 3; ++c) {
+                st.En[c] = hist(m, c);
+                st.En1[c] = hist(m + 1, c);
+            }
+            st.probe_comp = h->R.comp[probe];
+            st.probe_q = h->R.q[probe];
+            st.probe_src = 0.f;
+            if (n >= n0) {   // dJ/dE^n = 2 dt Re(conj(X) exp(-i 2 pi f dt n))
+                double ph = f * h->dt * (double)n;
+                ph -= floor(ph);
+                const double ang = 6.283185307179586476925286766559 * ph;
+                st.probe_src = (float)(2.0 * h->dt * (xr * cos(ang) - xi * sin(ang)));
+            }
+            const double t1 = (double)(n + 1) * h->dt;
+            for (int q = 0; q < h->nsrc; ++q) src.amp[q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
+            TF_CUDA(launch_adjoint_step(h->P, S, src, st, h->stream));
+        }
+    }
+    TF_CUDA(launch_adjoint_cells(h->P, S, (float)(kC0 * h->dt), grad_eps, grad_lambda, h->stream));
+    // leave the handle in the state the forward run reached
+    if ((rc = tf_checkpoint_load(h, sc + A.off_ck + A.nseg * A.ck, A.ck, 1)) != TF_OK) return rc;
+    TF_CUDA(cudaStreamSynchronize(h->stream));
+    return TF_OK;
+}
+
 tf_status tf_field_stats(tf_handle h, int comp, double* sumsq, double* maxabs, int64_t* nonfinite) {
     if (!h || comp < 0 || comp > 8) return TF_EINVAL;
     const float* f = comp < 3 ? h->P.E[comp] : comp < 6 ? h->P.B[comp - 3] : h->P.J[comp - 6];

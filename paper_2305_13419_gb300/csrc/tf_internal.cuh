@@ -244,6 +244,29 @@ cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, co
 cudaError_t launch_edge_coeffs(const Params& P, cudaStream_t st);
 size_t step_smem_bytes();
 cudaError_t launch_tile_materials(const Params& P, float4* tilemat, int ntx, int nty, cudaStream_t st);
+// discrete adjoint (tf_adjoint.cu): the adjoint state, in the scaled units of
+// the step, and per-edge gradient sums (FP64)
+struct AdjState {
+    float* E[3];
+    float* B[3];
+    float* J[3];
+    float* psiB[3][3];   // [component][axis], nullptr without CPML on the axis
+    float* psiE[3][3];
+    double* gE[3];       // dJ / d eps_r,e
+    double* gK[3];       // dJ / d kt_e
+};
+struct AdjStep {
+    const float* En[3];    // E^n
+    const float* En1[3];   // E^{n+1} (with this step's soft sources)
+    int probe_comp;        // the objective's derivative dJ/dE^n at the probe point
+    long long probe_q;
+    float probe_src;
+};
+cudaError_t launch_adjoint_step(const Params& P, const AdjState& A, const Sources& S, const AdjStep& st,
+                                cudaStream_t stream);
+cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0, float* g_eps, float* g_lam,
+                                 cudaStream_t stream);
+
 // order in which k_step hands out its work items (items needing the full plane loop first)
 cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int* order, cudaStream_t st);
 int step_blocks_per_sm();

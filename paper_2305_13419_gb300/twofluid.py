@@ -27,7 +27,7 @@ EXPORTS = ["tf_workspace_size", "tf_create", "tf_destroy", "tf_storage_dims", "t
            "tf_set_materials", "tf_set_field", "tf_add_source", "tf_add_probe", "tf_step", "tf_sync",
            "tf_read_probe_dft", "tf_read_probe_series", "tf_read_field", "tf_fit_q", "tf_strerror",
            "tf_step_timed", "tf_field_stats", "tf_field_stats_noalloc", "tf_checkpoint_size",
-           "tf_checkpoint_save", "tf_checkpoint_load"]
+           "tf_checkpoint_save", "tf_checkpoint_load", "tf_adjoint_scratch_size", "tf_adjoint_run"]
 
 
 class TFError(RuntimeError):
@@ -91,7 +91,9 @@ def load(build_if_missing: bool = True):
                                                    C.POINTER(C.c_int64), vp]),
                        ("tf_checkpoint_size", [vp, C.POINTER(C.c_size_t)]),
                        ("tf_checkpoint_save", [vp, vp, C.c_size_t, C.c_int]),
-                       ("tf_checkpoint_load", [vp, vp, C.c_size_t, C.c_int])):
+                       ("tf_checkpoint_load", [vp, vp, C.c_size_t, C.c_int]),
+                       ("tf_adjoint_scratch_size", [vp, C.c_int64, C.c_int, C.POINTER(C.c_size_t)]),
+                       ("tf_adjoint_run", [vp, C.c_int64, C.c_int, C.c_int, C.c_int, vp, C.c_size_t, dp, vp, vp])):
         fn = getattr(L, name)
         fn.restype = st
         fn.argtypes = args
@@ -345,6 +347,25 @@ class Grid:
         p, dev = _ptr(blob)
         nbytes = blob.numel() * blob.element_size() if hasattr(blob, "numel") else blob.nbytes
         _check(load().tf_checkpoint_load(self.h, p, int(nbytes), dev), "tf_checkpoint_load")
+
+    def adjoint(self, nsteps: int, probe: int = 0, freq_index: int = 0, segment: int = 256):
+        """J = |X|^2 of probe `probe`'s DFT at `freq_index` after nsteps from rest,
+        and dJ/d eps_r, dJ/d lambda_L per cell (CUDA tensors [nz][ny][nx]),
+        by the discrete adjoint with checkpoints every `segment` steps."""
+        import torch
+        n = C.c_size_t()
+        _check(load().tf_adjoint_scratch_size(self.h, int(nsteps), int(segment), C.byref(n)),
+               "tf_adjoint_scratch_size")
+        scratch = torch.empty(int(n.value), dtype=torch.uint8, device=self.device)
+        cs = (self.n[2], self.n[1], self.n[0])
+        ge = torch.empty(cs, dtype=torch.float32, device=self.device)
+        gl = torch.empty(cs, dtype=torch.float32, device=self.device)
+        J = C.c_double()
+        _check(load().tf_adjoint_run(self.h, int(nsteps), int(probe), int(freq_index), int(segment),
+                                     C.c_void_p(scratch.data_ptr()), int(n.value), C.byref(J),
+                                     C.c_void_p(ge.data_ptr()), C.c_void_p(gl.data_ptr())), "tf_adjoint_run")
+        del scratch
+        return J.value, ge, gl
 
     def fit_q(self, pid: int, f_guess: float = 0.0, q_guess: float = 100.0):
         f0, al, q = C.c_double(), C.c_double(), C.c_double()

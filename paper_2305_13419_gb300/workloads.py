@@ -307,6 +307,27 @@ def cpw_large(nsteps: int = 50000, **kw) -> Workload:
     return cpw(**args)
 
 
+def cpw_adjoint(nsteps: int = 8000, seed: int = BASE_SEED + 4, **kw) -> Workload:
+    """The adjoint workload: a 256 x 128 x 64 CPW (the config-2 template at
+    half size: CPML 12, 16-cell substrate, 2-cell films, 8-wide strip) whose
+    substrate eps_r is drawn per cell from U[10, 13]; the objective is |X|^2
+    of probe 0's DFT at the template's resonance estimate f0 (frequency
+    index 0 of a one-frequency probe)."""
+    args = dict(n=(256, 128, 64), pml=12, margin=4, substrate_cells=16, film_cells=2, strip_w=8, gap_w=4,
+                lam_cells=3.0, nsteps=nsteps, seed=seed)
+    args.update(kw)
+    w = cpw(**args)
+    rng = np.random.Generator(np.random.PCG64(seed + 100))
+    z_sub = args["pml"] + args["substrate_cells"]
+    w.eps_r = np.asarray(w.eps_r, np.float32).copy()
+    w.eps_r[:z_sub] = rng.uniform(10.0, 13.0, size=w.eps_r[:z_sub].shape).astype(np.float32)
+    f0 = w.sources[0].f
+    for p in w.probes:
+        p.freqs = np.array([f0])
+    w.name = "cpw-adjoint-" + "x".join(map(str, w.n))
+    return w
+
+
 def random_box(n=(9, 7, 11), bc=("periodic", "periodic", "periodic"), seed: int = 1,
                d=(10e-9, 12e-9, 8e-9), courant: float = 0.9, theta: float = 0.5,
                sc_fraction: float = 0.5, lam_range=(30e-9, 60e-9), sigma_range=(0.0, 1e6),
