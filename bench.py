@@ -347,18 +347,22 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(w, budget_s=args.cpu_budget)
 
-    adj = None
-    if rank == 0 and not args.no_adjoint:
+    adj = batch = None
+    if rank == 0 and (not args.no_adjoint or not args.no_batch):
         g.close()
         del g
+    if rank == 0 and not args.no_adjoint:
         adj = run_adjoint(args)
+    if rank == 0 and not args.no_batch:
+        batch = run_batch(args, value / ws)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_block(state_bytes), "roofline": roof, "cpu_baseline": base, "e2e": e2e,
-                "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "adjoint": adj}
+                "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "adjoint": adj,
+                "batched": batch}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -394,6 +398,40 @@ def run_adjoint(args):
             "gcell_updates_per_s": w.ncells * args.adjoint_steps / (ms * 1e-3) / 1e9,
             "objective": J, "grad_eps_absmax": float(ge.abs().max()), "grad_lambda_absmax": float(gl.abs().max()),
             "includes": "forward with checkpoints, per-segment recompute, adjoint steps, gradient reduction"}
+
+
+def run_batch(args, plain_gcells):
+    """The batched workload: 64 CPW variants with axes from {96, 128, 160},
+    stepped together by tf_batch_step with the grids spread over 8 streams,
+    and, for comparison, the same grids on one stream."""
+    import time
+    import torch
+    from paper_2305_13419_gb300 import twofluid as tf
+    from paper_2305_13419_gb300 import workloads as W
+    ws = W.cpw_batch()
+    cells = sum(w.ncells for w in ws)
+    out = {"grids": len(ws), "cells": cells, "steps": args.batch_steps, "sizes": [96, 128, 160]}
+    for nstreams in (8, 1):
+        streams = [torch.cuda.Stream() for _ in range(nstreams)]
+        grids = [tf.Grid.from_workload(w, stream=streams[i % nstreams]) for i, w in enumerate(ws)]
+        tf.batch_step(grids, 10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tf.batch_step(grids, args.batch_steps)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        for gg in grids:
+            gg.sync()
+            gg.close()
+        del grids
+        torch.cuda.empty_cache()
+        key = "streams8" if nstreams == 8 else "one_stream"
+        out[key] = {"ms_per_step": ms / args.batch_steps,
+                    "gcell_updates_per_s": cells * args.batch_steps / (ms * 1e-3) / 1e9}
+    out["gcell_updates_per_s"] = out["streams8"]["gcell_updates_per_s"]
+    out["vs_plain_step"] = out["gcell_updates_per_s"] / plain_gcells
+    out["timing"] = "host wall clock around the enqueue of all steps, device synchronised on both sides"
+    return out
 
 
 def run_e2e(args, w, dev):
@@ -444,6 +482,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--adjoint-steps", type=int, default=8000)
     args = ap.parse_args(argv)
     ws, rank, local = dist_env()

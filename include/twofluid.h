@@ -170,6 +170,14 @@ tf_status tf_step(tf_handle h, int64_t nsteps);
  * 1 fused step (arrays of nkinds <= 2 entries). */
 tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds);
 
+/* Advance n independent grids by nsteps steps each (the batched workload:
+ * many resonator variants at once).  The grids advance together, one step
+ * of every grid in turn; each grid's work goes to its own handle's stream,
+ * so grids on different streams overlap (one grid's last work items run
+ * beside the next grid's first ones).  Handles must be distinct; the call
+ * returns after enqueueing (use tf_sync per handle). */
+tf_status tf_batch_step(const tf_handle* hs, int n, int64_t nsteps);
+
 /* Wait for the stream and return the latched device status
  * (TF_ENONFINITE if the watchdog saw a non-finite E). */
 tf_status tf_sync(tf_handle h);

@@ -338,8 +338,11 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
             delete h;
             return TF_ECUDA;
         }
-        long long nb = (long long)sms * per_sm;
-        h->step_blocks = (int)(nb < items ? nb : items);
+        // one resident CTA per slot, but no more than half the items: a small
+        // grid then leaves SMs to grids stepping on other streams
+        long long nb = (long long)sms * per_sm, half = (items + 1) / 2;
+        if (half < nb) nb = half;
+        h->step_blocks = (int)(nb > 0 ? nb : 1);
     }
     // zero everything but the profiles, then vacuum materials
     cudaError_t e = cudaMemsetAsync(base + L.off_fields, 0, L.off_prof - L.off_fields, h->stream);
@@ -547,6 +550,42 @@ tf_status tf_step(tf_handle h, int64_t nsteps) {
     fill_sources(h, S);
     TF_CUDA(refresh_order(h, S));
     for (int64_t s = 0; s < nsteps; ++s) TF_CUDA(launch_one_step(h, S, nullptr));
+    return TF_OK;
+}
+
+tf_status tf_batch_step(const tf_handle* hs, int n, int64_t nsteps) {
+    if (!hs || n < 1 || nsteps < 0) return TF_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) return TF_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return TF_EINVAL;   // a handle twice would race with itself
+    }
+    if (nsteps == 0) return TF_OK;
+    Sources S[64];
+    const int chunk = n < 64 ? n : 64;
+    for (int b0 = 0; b0 < n; b0 += chunk) {
+        const int nb = (n - b0) < chunk ? (n - b0) : chunk;
+        for (int i = 0; i < nb; ++i) {
+            tf_ctx* h = hs[b0 + i];
+            if (!h->primed) {
+                TF_CUDA(launch_prime(h->P, h->stream));
+                h->primed = 1;
+            }
+            fill_sources(h, S[i]);
+            TF_CUDA(refresh_order(h, S[i]));
+        }
+    }
+    // step by step, every grid in turn: each grid's launches stay in order on
+    // its own stream while the grids' streams overlap one another's tails
+    for (int64_t s = 0; s < nsteps; ++s)
+        for (int b0 = 0; b0 < n; b0 += chunk) {
+            const int nb = (n - b0) < chunk ? (n - b0) : chunk;
+            for (int i = 0; i < nb; ++i) {
+                tf_ctx* h = hs[b0 + i];
+                if (n > 64) fill_sources(h, S[i]);
+                TF_CUDA(launch_one_step(h, S[i], nullptr));
+            }
+        }
     return TF_OK;
 }
 

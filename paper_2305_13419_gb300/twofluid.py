@@ -27,7 +27,7 @@ EXPORTS = ["tf_workspace_size", "tf_create", "tf_destroy", "tf_storage_dims", "t
            "tf_set_materials", "tf_set_field", "tf_add_source", "tf_add_probe", "tf_step", "tf_sync",
            "tf_read_probe_dft", "tf_read_probe_series", "tf_read_field", "tf_fit_q", "tf_strerror",
            "tf_step_timed", "tf_field_stats", "tf_field_stats_noalloc", "tf_checkpoint_size",
-           "tf_checkpoint_save", "tf_checkpoint_load", "tf_adjoint_scratch_size", "tf_adjoint_run"]
+           "tf_checkpoint_save", "tf_checkpoint_load", "tf_adjoint_scratch_size", "tf_adjoint_run", "tf_batch_step"]
 
 
 class TFError(RuntimeError):
@@ -93,7 +93,8 @@ def load(build_if_missing: bool = True):
                        ("tf_checkpoint_save", [vp, vp, C.c_size_t, C.c_int]),
                        ("tf_checkpoint_load", [vp, vp, C.c_size_t, C.c_int]),
                        ("tf_adjoint_scratch_size", [vp, C.c_int64, C.c_int, C.POINTER(C.c_size_t)]),
-                       ("tf_adjoint_run", [vp, C.c_int64, C.c_int, C.c_int, C.c_int, vp, C.c_size_t, dp, vp, vp])):
+                       ("tf_adjoint_run", [vp, C.c_int64, C.c_int, C.c_int, C.c_int, vp, C.c_size_t, dp, vp, vp]),
+                       ("tf_batch_step", [C.POINTER(vp), C.c_int, C.c_int64])):
         fn = getattr(L, name)
         fn.restype = st
         fn.argtypes = args
@@ -171,6 +172,13 @@ def tf_field_stats_noalloc(field, nx_pts, ny_pts, nz_pts, pitch, scale=1.0, stre
                                          float(scale), C.byref(s), C.byref(m), C.byref(n),
                                          C.c_void_p(stream)), "tf_field_stats_noalloc")
     return s.value, m.value, int(n.value)
+
+
+def batch_step(grids, nsteps: int):
+    """Advance every grid of `grids` by nsteps (tf_batch_step): the grids'
+    launches interleave on their own streams."""
+    hs = (C.c_void_p * len(grids))(*[g.h for g in grids])
+    _check(load().tf_batch_step(hs, len(grids), int(nsteps)), "tf_batch_step")
 
 
 def _ptr(buf):

@@ -328,6 +328,33 @@ def cpw_adjoint(nsteps: int = 8000, seed: int = BASE_SEED + 4, **kw) -> Workload
     return w
 
 
+def cpw_batch(count: int = 64, seed: int = BASE_SEED + 3, nsteps: int = 8000, sizes=(96, 128, 160)):
+    """The batched workload: `count` CPW resonator variants, each axis drawn
+    independently from `sizes`; the config-2 template scaled to each grid
+    (CPML, margin, substrate and film thickness in proportion to the axis),
+    strip and gap widths drawn from U{4..16}, lambda_L from U[2, 6] cells and
+    sigma_n per metal cell from U[0, 1e6] S/m."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        nx, ny, nz = (int(rng.choice(sizes)) for _ in range(3))
+        pml = max(6, round(12 * min(nx, ny, nz) / 128))
+        margin = max(2, round(4 * min(nx, ny, nz) / 128))
+        sub = max(8, round(32 * nz / 128))
+        film = max(2, round(4 * nz / 128))
+        free_y = ny - 2 * (pml + margin)
+        strip = int(rng.integers(4, 17))
+        gap = int(rng.integers(4, 17))
+        while strip + 2 * gap > free_y - 4:   # keep ground planes on both sides
+            strip, gap = max(4, strip - 2), max(4, gap - 2)
+        lam = float(rng.uniform(2.0, 6.0))
+        w = cpw(n=(nx, ny, nz), pml=pml, margin=margin, substrate_cells=sub, film_cells=film, strip_w=strip,
+                gap_w=gap, lam_cells=lam, nsteps=nsteps, seed=seed * 1000 + i)
+        w.name = f"cpw-batch-{i}-{nx}x{ny}x{nz}"
+        out.append(w)
+    return out
+
+
 def random_box(n=(9, 7, 11), bc=("periodic", "periodic", "periodic"), seed: int = 1,
                d=(10e-9, 12e-9, 8e-9), courant: float = 0.9, theta: float = 0.5,
                sc_fraction: float = 0.5, lam_range=(30e-9, 60e-9), sigma_range=(0.0, 1e6),
