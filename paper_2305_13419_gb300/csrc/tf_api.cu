@@ -54,6 +54,9 @@ tf_status validate(const tf_grid_desc* d) {
     if (d->max_probes < 0 || d->max_probes > TF_MAX_PROBES || d->series_capacity < 0) return TF_EINVAL;
     const long long pts = (long long)(n[0] + 1) * (n[1] + 1) * (n[2] + 1);
     if (pts > (1LL << 40)) return TF_EINVAL;
+    // work-item descriptors hold 16 bits of tile index and 12 bits of plane
+    const long long tx = (n[0] + 1 + kSX - 1) / kSX, ty = (n[1] + 1 + kSY - 1) / kSY;
+    if (tx * ty > kMaxTiles || n[2] + 1 > kMaxPlanes) return TF_ENOTSUP;
     return TF_OK;
 }
 
@@ -90,7 +93,7 @@ Layout layout_of(const tf_grid_desc* d) {
     L.scratch_floats = 4 * L.ncell > L.ndense ? 4 * L.ncell : L.ndense;
     L.off_scratch = o; o += align_up(sizeof(float) * (size_t)L.scratch_floats);
     L.off_tiles = o;  o += align_up(sizeof(float4) * (size_t)L.ntx * L.nty * L.N[2]);
-    L.off_order = o;  o += align_up(sizeof(int) * (size_t)L.ntx * L.nty * L.nch);
+    L.off_order = o;  o += align_up(sizeof(int) * (size_t)L.ntx * L.nty * L.nch * ((kChunk + kSub - 1) / kSub));
     L.off_stats = o;  o += align_up(sizeof(StatPartial) * (size_t)(L.N[2] + 1));
     L.off_misc = o;   o += kAlign;
     L.bytes = o;
@@ -509,7 +512,7 @@ cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
     h->O.psib_cur = h->parity ? 2 : 0;
     h->O.ecur = h->parity ? 9 : 0;
     h->O.bcur = h->parity ? 12 : 3;
-    h->O.base += (unsigned long long)h->L.ntx * h->L.nty * h->L.nch + (unsigned long long)h->step_blocks;
+    h->O.base += (unsigned long long)h->O.nitems + (unsigned long long)h->step_blocks;
     h->level++;
     return e;
 }
@@ -517,9 +520,18 @@ cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
 // rebuild the work-item order after the sources or materials changed
 cudaError_t refresh_order(tf_ctx* h, const Sources& S) {
     if (!h->order_dirty) return cudaSuccess;
-    const cudaError_t e = launch_item_order(h->P, h->O, S, (int*)h->O.order, h->stream);
-    if (e == cudaSuccess) h->order_dirty = 0;
-    return e;
+    int* dcount = (int*)(h->ws + h->L.off_misc + 192);
+    // fewer than 8 (tile, chunk) items per CTA: cut the slow ones into pieces
+    const long long items = (long long)h->L.ntx * h->L.nty * h->L.nch;
+    const int split = items < 8LL * h->step_blocks;
+    cudaError_t e = launch_item_order(h->P, h->O, S, split, (int*)h->O.order, dcount, h->stream);
+    int n = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n, dcount, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return e;
+    h->O.nitems = n;
+    h->order_dirty = 0;
+    return cudaSuccess;
 }
 
 void fill_sources(const tf_ctx* h, Sources& S) {

@@ -73,6 +73,9 @@ constexpr int kEX = kTX + 8, kEY = kTY + 2;  // E box: x0-4 .. x0+35, y0-1 .. y0
 constexpr int kBX = kTX + 4, kBY = kTY + 1;  // B / psi_B box: x0-4 .. x0+31, y0-1 .. y0+kTY-1
 constexpr int kStages = 4;                   // planes in flight per CTA
 constexpr int kChunk = 8;                    // z planes per work item
+constexpr int kSub = 2;                      // planes per piece of a work item that takes the full loop
+// a work item is a descriptor: tile (bits 0-15), first plane (16-27), planes - 1 (28-31)
+constexpr int kMaxTiles = 1 << 16, kMaxPlanes = 1 << 12;
 constexpr long long kSpinLimit = 1LL << 22;  // bounded mbarrier waits
 
 struct StepOut {
@@ -86,7 +89,8 @@ struct StepOut {
     int ecur, bcur;          // index of the current E / B arrays in the field tensor map
     int psi_slot[3];         // per axis: group of 6 psi arrays in the psi tensor map, -1 if no CPML
     int psib_cur;            // 0 or 2: current psi_B pair inside a group (E pair at 4)
-    const int* order;        // work items of a launch in the order they are handed out
+    const int* order;        // work-item descriptors of a launch in the order they are handed out
+    int nitems;              // descriptors in `order`
     unsigned long long* ctr; // work counter (monotone across launches)
     unsigned long long base; // counter value at the start of this launch
 };
@@ -268,7 +272,8 @@ cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0
                                  cudaStream_t stream);
 
 // order in which k_step hands out its work items (items needing the full plane loop first)
-cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int* order, cudaStream_t st);
+cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int* order,
+                              int* count, cudaStream_t st);
 int step_blocks_per_sm();
 cudaError_t launch_field_stats(const float* f, int n0, int n1, int n2, int pitch, long long plane, double scale,
                                StatPartial* partials, StatPartial* out, cudaStream_t st);

@@ -133,17 +133,19 @@ struct Tile {
 };
 __device__ __forceinline__ Tile tile_of(const Params& P, const StepOut& O, int item) {
     Tile t;
-    const int ch = item % O.nch;   // consecutive items: consecutive chunks of one tile
-    const int tile = item / O.nch;
+    const int tile = item & 0xffff;   // descriptor: tile, first plane, planes - 1
     t.bx = tile % O.ntx;
     t.by = tile / O.ntx;
     t.x0 = t.bx * kSX;
     t.y0 = t.by * kSY;
-    t.kz0 = ch * kChunk;
-    t.kz1 = min(t.kz0 + kChunk, O.kend);
+    t.kz0 = (item >> 16) & 0xfff;
+    t.kz1 = t.kz0 + ((unsigned)item >> 28) + 1;
     t.ks = (t.kz0 > 0 || P.per[2]) ? t.kz0 - 1 : t.kz0;
     t.nq = t.kz1 - t.ks + 1;   // planes pulled: ks .. kz1
     return t;
+}
+__device__ __forceinline__ int make_item(int tile, int kz0, int len) {
+    return (int)((unsigned)tile | (unsigned)kz0 << 16 | (unsigned)(len - 1) << 28);
 }
 __device__ __forceinline__ int plane_of(const Params& P, const Tile& t, int q) {
     int k = t.ks + q;
@@ -228,6 +230,11 @@ __device__ __forceinline__ void st2m(float* p, f2 v, unsigned m) {
 struct P3 {
     f2 x, y, z;
 };
+
+// bring the line holding p into L1 (no register, no wait)
+__device__ __forceinline__ void prefetch_l1(const float* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 
 // update masks of a pair of points (gx0, gx0 + 1) on row gy: per point p, bits
 // 6p + {0, 1, 2} for Bx, By, Bz and 6p + {3, 4, 5} for Ex, Ey, Ez (x / y walls)
@@ -361,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ float4 s_rec[2][kChunk + 2];     // material record of each plane of the two items
     __shared__ unsigned s_flag[2][kChunk + 2];  // plane flags
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
-    const int nitems = O.ntx * O.nty * O.nch;
+    const int nitems = O.nitems;
     const int PL = (int)P.plane;
     const bool mur = P.bc[2] == TF_BC_MUR;
 
@@ -600,6 +607,26 @@ __global__ void __launch_bounds__(kThreads, 2)
                     }
                     hbB = pk(e0, e1);
                     hcB = pk(h0, h1);
+                }
+            }
+            if (kRare && sec) {   // CPML memories of the further slab axes: into L1 while the stage lands
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (!((sec >> a) & 1u)) continue;
+                    if (v0) {
+                        prefetch_l1(P.psiB[pair_c1(a)][a] + q);
+                        prefetch_l1(P.psiB[pair_c2(a)][a] + q);
+                        prefetch_l1(P.psiE[pair_c1(a)][a] + q);
+                        prefetch_l1(P.psiE[pair_c2(a)][a] + q);
+                    }
+                    if (hal) {
+                        const int xw = wrap_or_out(P, 0, hgx0), yw = wrap_or_out(P, 1, hgy);
+                        if (xw >= 0 && yw >= 0) {
+                            const int qh = kq + yw * P.pitch + xw;
+                            prefetch_l1(P.psiB[pair_c1(a)][a] + qh);
+                            prefetch_l1(P.psiB[pair_c2(a)][a] + qh);
+                        }
+                    }
                 }
             }
             bool ok = mbar_wait(&bar[g1 % kStages], (unsigned)((g1 / kStages) & 1));
@@ -989,38 +1016,62 @@ cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, co
     return cudaGetLastError();
 }
 
-// order of the work items of a launch: a stable partition that puts the items
-// needing the full plane loop (the slow ones) first, so that the last items
-// handed out are short.  One CTA.
-__global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Sources S, int* order) {
-    __shared__ int sc[1024];
+// work items of a launch, in the order they are handed out: the (tile, z
+// chunk) items that need the full plane loop come first -- on a grid with
+// few items per CTA (`split`) each cut into kSub-plane pieces, so that their
+// long bodies run side by side -- then the others, whole.  One CTA; writes
+// the descriptors and their count.
+__global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Sources S, int split, int* order,
+                                                    int* count) {
+    __shared__ int s_slow[1024], s_fast[1024];
     const int n = O.ntx * O.nty * O.nch;
     const int per = (n + 1023) / 1024;
     const int a = min((int)threadIdx.x * per, n), b = min(a + per, n);
     const bool mur = P.bc[2] == TF_BC_MUR;
-    int cnt = 0;
-    for (int d = a; d < b; ++d) cnt += item_is_rare(P, S, mur, tile_of(P, O, d)) ? 1 : 0;
-    sc[threadIdx.x] = cnt;
+    auto chunk = [&](int d, int& tile, int& kz0, int& len) {
+        tile = d / O.nch;
+        kz0 = (d % O.nch) * kChunk;
+        len = min(kChunk, O.kend - kz0);
+    };
+    int ns = 0, nf = 0;
+    for (int d = a; d < b; ++d) {
+        int tile, kz0, len;
+        chunk(d, tile, kz0, len);
+        if (item_is_rare(P, S, mur, tile_of(P, O, make_item(tile, kz0, len))))
+            ns += split ? (len + kSub - 1) / kSub : 1;
+        else
+            nf += 1;
+    }
+    s_slow[threadIdx.x] = ns;
+    s_fast[threadIdx.x] = nf;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
-        const int v = (int)threadIdx.x >= off ? sc[threadIdx.x - off] : 0;
+        const int vs = (int)threadIdx.x >= off ? s_slow[threadIdx.x - off] : 0;
+        const int vf = (int)threadIdx.x >= off ? s_fast[threadIdx.x - off] : 0;
         __syncthreads();
-        sc[threadIdx.x] += v;
+        s_slow[threadIdx.x] += vs;
+        s_fast[threadIdx.x] += vf;
         __syncthreads();
     }
-    const int total = sc[1023];
-    int r = sc[threadIdx.x] - cnt;   // rare items before this thread's range
-    int c = total + (a - r);         // position of its first common item
+    const int total_slow = s_slow[1023];
+    int r = s_slow[threadIdx.x] - ns;                // slow pieces before this thread's range
+    int c = total_slow + s_fast[threadIdx.x] - nf;   // position of its first whole item
     for (int d = a; d < b; ++d) {
-        if (item_is_rare(P, S, mur, tile_of(P, O, d)))
-            order[r++] = d;
-        else
-            order[c++] = d;
+        int tile, kz0, len;
+        chunk(d, tile, kz0, len);
+        if (item_is_rare(P, S, mur, tile_of(P, O, make_item(tile, kz0, len)))) {
+            const int piece = split ? kSub : len;
+            for (int k = kz0; k < kz0 + len; k += piece) order[r++] = make_item(tile, k, min(piece, kz0 + len - k));
+        } else {
+            order[c++] = make_item(tile, kz0, len);
+        }
     }
+    if (threadIdx.x == 1023) *count = total_slow + s_fast[1023];
 }
 
-cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int* order, cudaStream_t st) {
-    k_item_order<<<1, 1024, 0, st>>>(P, O, S, order);
+cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int* order,
+                              int* count, cudaStream_t st) {
+    k_item_order<<<1, 1024, 0, st>>>(P, O, S, split, order, count);
     return cudaGetLastError();
 }
 
