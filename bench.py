@@ -434,6 +434,60 @@ def run_batch(args, plain_gcells):
     return out
 
 
+def run_precision_study(args):
+    """FP32 fused step against the FP64 stepper on the same CPW over a long
+    run: relative L2 of each field family (against the family's peak norm
+    over the run, as the ring-down decays) at checkpoints, and of both
+    probes' spectra at the end.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_2305_13419_gb300 import twofluid as tf
+    from paper_2305_13419_gb300 import workloads as W
+    w = W.cpw_large(nsteps=args.fp64_study) if args.study_workload == "cpw_large" else W.cpw(nsteps=args.fp64_study)
+    g32 = tf.Grid.from_workload(w)
+    g64 = tf.Grid64.from_workload(w)
+    fams = (("E", 0), ("B", 3), ("Js", 6))
+    peak = {k: 0.0 for k, _ in fams}
+    rows = []
+    marks = sorted(set(int(round(args.fp64_study * f)) for f in (0.1, 0.25, 0.5, 0.75, 1.0)))
+    done = 0
+    t32 = t64 = 0.0
+    for m in marks:
+        for gg, which in ((g32, 32), (g64, 64)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gg.step(m - done)
+            gg.sync()
+            dt_ = time.perf_counter() - t0
+            if which == 32:
+                t32 += dt_
+            else:
+                t64 += dt_
+        done = m
+        row = {"step": m}
+        for name, f in fams:
+            d2 = r2 = 0.0
+            for c in range(f, f + 3):
+                a = g32.field(c).astype(np.float64)
+                b = g64.field(c)
+                d2 += float(np.sum((a - b) ** 2))
+                r2 += float(np.sum(b * b))
+            peak[name] = max(peak[name], r2 ** 0.5)
+            row[name] = d2 ** 0.5 / peak[name] if peak[name] > 0 else 0.0
+        rows.append(row)
+    spec = []
+    for p in range(len(w.probes)):
+        x, y = g32.probe_dft(p), g64.probe_dft(p)
+        spec.append(float(np.linalg.norm(x - y) / np.linalg.norm(y)))
+    cells = w.ncells
+    line = {"study": "fp32 fused step vs fp64 stepper", "workload": w.name, "steps": args.fp64_study,
+            "field_rel_l2_vs_peak": rows, "probe_spectrum_rel_l2": spec,
+            "fp32_gcell_updates_per_s": cells * args.fp64_study / t32 / 1e9,
+            "fp64_gcell_updates_per_s": cells * args.fp64_study / t64 / 1e9}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_e2e(args, w, dev):
     """Same metric through the public API from host memory: the timed region
     uploads the material maps from pinned host buffers, runs the K steps and
@@ -483,6 +537,8 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--fp64-study", type=int, default=0, help="run only the FP32-vs-FP64 study over this many steps")
+    ap.add_argument("--study-workload", choices=("cpw", "cpw_large"), default="cpw")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--adjoint-steps", type=int, default=8000)
     args = ap.parse_args(argv)
@@ -491,6 +547,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.fp64_study > 0:
+        return run_precision_study(args)
     return run_ours(args, ws, rank, local)
 
 

@@ -277,6 +277,33 @@ tf_status tf_field_stats(tf_handle h, int comp, double* sumsq, double* maxabs, i
 tf_status tf_field_stats_noalloc(const float* field, int nx_pts, int ny_pts, int nz_pts, int pitch, double scale,
                                  double* sumsq, double* maxabs, int64_t* nonfinite, void* stream);
 
+/* FP64 stepper: the precision reference of the FP32 path (the study of how
+ * far FP32 fields drift over long runs).  Runs Algorithm 1 (Sec. 3) as its
+ * five sub-steps in FP64 and SI units on the integer-level state, with the
+ * same edge/face material rule, boundaries (periodic, PEC, CPML, Mur on z),
+ * soft sources and FP64 probe DFTs as the FP32 path.  Fields are dense
+ * float64 [Nz][Ny][Nx] (no row padding), host buffers; materials dense
+ * float64 [nz][ny][nx] on the host.  Same descriptor as tf_create; the
+ * workspace is caller-owned device memory (256-byte aligned) of
+ * tf64_workspace_size bytes.  tf64_step enqueues on the descriptor's
+ * stream; reads synchronise it.  Errors as for the FP32 calls. */
+typedef struct tf64_ctx* tf64_handle;
+size_t tf64_workspace_size(const tf_grid_desc* desc);
+tf_status tf64_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes, tf64_handle* out);
+tf_status tf64_destroy(tf64_handle h);
+tf_status tf64_set_materials(tf64_handle h, const double* eps_r, const double* mu_r, const double* lambda_L,
+                             const double* sigma);
+tf_status tf64_set_field(tf64_handle h, int comp, const double* src);
+tf_status tf64_add_source(tf64_handle h, int comp, const int lo[3], const int hi[3], double amp, int kind,
+                          double f, double t0, double tw, int* id);
+tf_status tf64_add_probe(tf64_handle h, int comp, const int p[3], const double* freqs, int nfreq, int64_t n0,
+                         int* id);
+tf_status tf64_step(tf64_handle h, int64_t nsteps);
+tf_status tf64_sync(tf64_handle h);
+tf_status tf64_read_field(tf64_handle h, int comp, double* dst);
+tf_status tf64_read_probe_dft(tf64_handle h, int id, double* re, double* im);
+tf_status tf64_get_time(tf64_handle h, int64_t* n, double* dt);
+
 const char* tf_strerror(tf_status s);
 
 #ifdef __cplusplus

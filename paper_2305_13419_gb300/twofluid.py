@@ -27,7 +27,10 @@ EXPORTS = ["tf_workspace_size", "tf_create", "tf_destroy", "tf_storage_dims", "t
            "tf_set_materials", "tf_set_field", "tf_add_source", "tf_add_probe", "tf_step", "tf_sync",
            "tf_read_probe_dft", "tf_read_probe_series", "tf_read_field", "tf_fit_q", "tf_strerror",
            "tf_step_timed", "tf_field_stats", "tf_field_stats_noalloc", "tf_checkpoint_size",
-           "tf_checkpoint_save", "tf_checkpoint_load", "tf_adjoint_scratch_size", "tf_adjoint_run", "tf_batch_step"]
+           "tf_checkpoint_save", "tf_checkpoint_load", "tf_adjoint_scratch_size", "tf_adjoint_run", "tf_batch_step",
+           "tf64_workspace_size", "tf64_create", "tf64_destroy", "tf64_set_materials", "tf64_set_field",
+           "tf64_add_source", "tf64_add_probe", "tf64_step", "tf64_sync", "tf64_read_field", "tf64_read_probe_dft",
+           "tf64_get_time"]
 
 
 class TFError(RuntimeError):
@@ -94,10 +97,21 @@ def load(build_if_missing: bool = True):
                        ("tf_checkpoint_load", [vp, vp, C.c_size_t, C.c_int]),
                        ("tf_adjoint_scratch_size", [vp, C.c_int64, C.c_int, C.POINTER(C.c_size_t)]),
                        ("tf_adjoint_run", [vp, C.c_int64, C.c_int, C.c_int, C.c_int, vp, C.c_size_t, dp, vp, vp]),
-                       ("tf_batch_step", [C.POINTER(vp), C.c_int, C.c_int64])):
+                       ("tf_batch_step", [C.POINTER(vp), C.c_int, C.c_int64]),
+                       ("tf64_create", [C.POINTER(tf_grid_desc), vp, C.c_size_t, C.POINTER(vp)]),
+                       ("tf64_destroy", [vp]), ("tf64_set_materials", [vp, vp, vp, vp, vp]),
+                       ("tf64_set_field", [vp, C.c_int, vp]),
+                       ("tf64_add_source", [vp, C.c_int, ip, ip, C.c_double, C.c_int, C.c_double, C.c_double,
+                                            C.c_double, ip]),
+                       ("tf64_add_probe", [vp, C.c_int, ip, dp, C.c_int, C.c_int64, ip]),
+                       ("tf64_step", [vp, C.c_int64]), ("tf64_sync", [vp]), ("tf64_read_field", [vp, C.c_int, vp]),
+                       ("tf64_read_probe_dft", [vp, C.c_int, dp, dp]),
+                       ("tf64_get_time", [vp, C.POINTER(C.c_int64), dp])):
         fn = getattr(L, name)
         fn.restype = st
         fn.argtypes = args
+    L.tf64_workspace_size.restype = C.c_size_t
+    L.tf64_workspace_size.argtypes = [C.POINTER(tf_grid_desc)]
     L.tf_strerror.restype = C.c_char_p
     L.tf_strerror.argtypes = [C.c_int]
     _lib = L
@@ -172,6 +186,102 @@ def tf_field_stats_noalloc(field, nx_pts, ny_pts, nz_pts, pitch, scale=1.0, stre
                                          float(scale), C.byref(s), C.byref(m), C.byref(n),
                                          C.c_void_p(stream)), "tf_field_stats_noalloc")
     return s.value, m.value, int(n.value)
+
+
+class Grid64:
+    """FP64 GPU stepper (Algorithm 1's sub-steps in FP64): the precision
+    reference of the FP32 path.  Dense float64 fields [Nz][Ny][Nx], SI."""
+
+    def __init__(self, n, d, theta=1.0, bc=("periodic",) * 3, cpml=(None, None, None), dt=None, courant=None,
+                 edge_rule=0, max_probes=TF_MAX_PROBES, device=None, stream=None):
+        import torch
+        load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("the FP64 stepper needs a CUDA device")
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.desc = make_desc(n, d, theta, bc, cpml, dt, courant, edge_rule, max_probes, 0, self.stream.cuda_stream)
+        nbytes = load().tf64_workspace_size(C.byref(self.desc))
+        if nbytes == 0:
+            raise TFError(TF_EINVAL, "tf64_workspace_size")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        h = C.c_void_p()
+        _check(load().tf64_create(C.byref(self.desc), C.c_void_p(base), nbytes, C.byref(h)), "tf64_create")
+        self.h = h
+        self.n = tuple(int(x) for x in n)
+        self.N = tuple(int(n[a]) + (0 if bc[a] == "periodic" else 1) for a in range(3))
+        self.shape = (self.N[2], self.N[1], self.N[0])
+        self.freqs = []
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        g = cls(w.n, w.d, w.theta, w.bc, w.cpml, dt=w.dt, courant=w.courant, edge_rule=getattr(w, "edge_rule", 0),
+                **kw)
+        g.set_materials(w.eps_r, w.mu_r, w.lambda_L, w.sigma)
+        for s in w.sources:
+            g.add_source(s.comp, s.lo, s.hi, s.amp, s.kind, s.f, s.t0, s.tw)
+        for p in w.probes:
+            g.add_probe(p.comp, p.p, p.freqs, p.n0)
+        return g
+
+    def set_materials(self, eps_r, mu_r, lambda_L, sigma):
+        cs = (self.n[2], self.n[1], self.n[0])
+        arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(x, np.float64), cs)) for x in
+                (eps_r, mu_r, lambda_L, sigma)]
+        _check(load().tf64_set_materials(self.h, *[a.ctypes.data for a in arrs]), "tf64_set_materials")
+
+    def set_field(self, comp, arr):
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(arr, np.float64), self.shape))
+        _check(load().tf64_set_field(self.h, int(comp), a.ctypes.data), "tf64_set_field")
+
+    def add_source(self, comp, lo, hi, amp, kind, f=0.0, t0=0.0, tw=1.0):
+        lo_ = (C.c_int * 3)(*[int(x) for x in lo])
+        hi_ = (C.c_int * 3)(*[int(x) for x in hi])
+        _check(load().tf64_add_source(self.h, int(comp), lo_, hi_, float(amp), int(kind), float(f), float(t0),
+                                      float(tw), None), "tf64_add_source")
+
+    def add_probe(self, comp, p, freqs, n0=0):
+        fr = np.ascontiguousarray(np.asarray(freqs, np.float64))
+        p_ = (C.c_int * 3)(*[int(x) for x in p])
+        _check(load().tf64_add_probe(self.h, int(comp), p_, fr.ctypes.data_as(C.POINTER(C.c_double)), int(fr.size),
+                                     int(n0), None), "tf64_add_probe")
+        self.freqs.append(fr)
+
+    def step(self, n):
+        _check(load().tf64_step(self.h, int(n)), "tf64_step")
+
+    def sync(self):
+        _check(load().tf64_sync(self.h), "tf64_sync")
+
+    def field(self, comp):
+        out = np.empty(self.shape, np.float64)
+        _check(load().tf64_read_field(self.h, int(comp), out.ctypes.data), "tf64_read_field")
+        return out
+
+    def probe_dft(self, pid):
+        nf = self.freqs[pid].size
+        re, im = np.zeros(max(nf, 1)), np.zeros(max(nf, 1))
+        _check(load().tf64_read_probe_dft(self.h, int(pid), re.ctypes.data_as(C.POINTER(C.c_double)),
+                                          im.ctypes.data_as(C.POINTER(C.c_double))), "tf64_read_probe_dft")
+        return (re + 1j * im)[:nf]
+
+    @property
+    def level(self):
+        n = C.c_int64()
+        _check(load().tf64_get_time(self.h, C.byref(n), None), "tf64_get_time")
+        return int(n.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().tf64_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def batch_step(grids, nsteps: int):

@@ -19,7 +19,7 @@ def _declared():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(tf_\w+)\s*\(", src, flags=re.M):
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(tf(?:64)?_\w+)\s*\(", src, flags=re.M):
             names.add(m.group(1))
     return names
 
@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
     names = _declared()
     assert {"tf_create", "tf_step", "tf_read_field", "tf_fit_q"} <= names
     out = subprocess.run(["nm", "-D", "--defined-only", tfbuild.LIB], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\b(tf_\w+)\b", out))
+    exported = set(re.findall(r"\b(tf(?:64)?_\w+)\b", out))
     assert names <= exported, names - exported
     for n in names:
         assert hasattr(lib, n)
