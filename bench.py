@@ -347,14 +347,17 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(w, budget_s=args.cpu_budget)
 
-    adj = batch = None
-    if rank == 0 and (not args.no_adjoint or not args.no_batch):
+    adj = batch = extra = None
+    if rank == 0 and (not args.no_adjoint or not args.no_batch or not args.no_configs):
         g.close()
         del g
     if rank == 0 and not args.no_adjoint:
         adj = run_adjoint(args)
     if rank == 0 and not args.no_batch:
         batch = run_batch(args, value / ws)
+    if rank == 0 and not args.no_configs:
+        extra = {"slab": run_config(W.slab(), 4000, 50),
+                 "large": run_config(W.cpw_large(), args.large_steps, 5)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -362,7 +365,7 @@ def run_ours(args, ws, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_block(state_bytes), "roofline": roof, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "adjoint": adj,
-                "batched": batch}
+                "batched": batch, "other_configs": extra}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -432,6 +435,69 @@ def run_batch(args, plain_gcells):
     out["vs_plain_step"] = out["gcell_updates_per_s"] / plain_gcells
     out["timing"] = "host wall clock around the enqueue of all steps, device synchronised on both sides"
     return out
+
+
+def run_config(w, steps, warmup=5):
+    """GPU throughput of the plain step on one workload: the whole step timed
+    with CUDA events on the handle's stream, and the step kernel's
+    algorithmic bytes over its own event-timed launches."""
+    import torch
+    from paper_2305_13419_gb300 import twofluid as tf
+    g = tf.Grid.from_workload(w)
+    g.step(warmup)
+    g.sync()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(g.stream)
+    g.step(steps)
+    stop.record(g.stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop) / steps
+    kt = g.step_timed(steps)
+    g.sync()
+    ab = algorithmic_bytes(w, g.N)
+    g.close()
+    peak, _ = hbm_peak()
+    achieved = ab["step"] / (kt["step"][0] * 1e-3) / 1e9
+    return {"workload": w.name, "cells": w.ncells, "steps": steps, "ms_per_step": ms,
+            "gcell_updates_per_s": w.ncells / (ms * 1e-3) / 1e9,
+            "roofline": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "algorithmic_bytes": ab["step"]}}
+
+
+def run_all_configs(args):
+    """Every config of the study side by side: GPU throughput (plain step;
+    adjoint and batch as in the default line) and the FP64 oracle on this
+    host's cores over a bounded sample of the same workload.  One JSON line."""
+    from oracle import stepper
+    from paper_2305_13419_gb300 import workloads as W
+    out = {}
+    slab = W.slab()
+    out["1_slab"] = {"gpu": run_config(slab, 4000, 50), "cpu_oracle": cpu_baseline(slab, budget_s=5.0)}
+    cpw = W.cpw()
+    out["2_cpw"] = {"gpu": run_config(cpw, 2000, 20), "cpu_oracle": cpu_baseline(cpw, budget_s=10.0)}
+    plain = out["2_cpw"]["gpu"]["gcell_updates_per_s"]
+    out["3_batch"] = {"gpu": run_batch(args, plain),
+                      "cpu_oracle": cpu_baseline(W.cpw_batch(count=1, sizes=(128,))[0], budget_s=10.0)}
+    adj_w = W.cpw_adjoint()
+    cpu_adj = cpu_baseline(adj_w, budget_s=10.0)
+    # the oracle adjoint (serial transposes) over a short window of the same grid
+    g = stepper.Grid.from_workload(adj_w, with_probes=False)
+    pr = adj_w.probes[0]
+    t0 = time.perf_counter()
+    g.adjoint_run(16, pr.comp, pr.p, float(pr.freqs[0]), 0)
+    el = time.perf_counter() - t0
+    cpu_adj["adjoint_forward_plus_backward_gcell_updates_per_s"] = adj_w.ncells * 16 / el / 1e9
+    out["4_adjoint"] = {"gpu": run_adjoint(args), "cpu_oracle": cpu_adj}
+    large = W.cpw_large()
+    sl = (slice(0, 128), slice(128, 384), slice(256, 512))
+    block = W.Workload(name="cpw-1024x512x256[256:512,128:384,0:128]", n=(256, 256, 128), d=large.d,
+                       theta=large.theta, bc=("pec", "pec", "pec"), eps_r=np.ascontiguousarray(large.eps_r[sl]),
+                       mu_r=np.ascontiguousarray(large.mu_r[sl]), lambda_L=np.ascontiguousarray(large.lambda_L[sl]),
+                       sigma=np.ascontiguousarray(large.sigma[sl]), courant=large.courant)
+    out["5_large"] = {"gpu": run_config(large, args.large_steps, 5), "cpu_oracle": cpu_baseline(block, budget_s=10.0)}
+    print(json.dumps({"all_configs": out}), flush=True)
+    return 0
 
 
 def run_precision_study(args):
@@ -537,6 +603,9 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--all-configs", action="store_true", help="per-config GPU and oracle numbers, one JSON line")
+    ap.add_argument("--large-steps", type=int, default=200)
     ap.add_argument("--fp64-study", type=int, default=0, help="run only the FP32-vs-FP64 study over this many steps")
     ap.add_argument("--study-workload", choices=("cpw", "cpw_large"), default="cpw")
     ap.add_argument("--batch-steps", type=int, default=200)
@@ -549,6 +618,8 @@ def main(argv=None):
         return run_reference(args, ws, rank)
     if args.fp64_study > 0:
         return run_precision_study(args)
+    if args.all_configs:
+        return run_all_configs(args)
     return run_ours(args, ws, rank, local)
 
 
