@@ -791,35 +791,36 @@ __global__ void __launch_bounds__(kThreads, 2)
                     cx = sub2(cx, q0);
                     cy = add2(cy, q1);
                 }
-                if (kRare && sec) {   // further slab axes, point by point
-                    float c3[3][2] = {{lo(cx), hi(cx)}, {lo(cy), hi(cy)}, {lo(cz), hi(cz)}};
-                    const f2 dh[6] = {dHz_x, dHy_x, dHz_y, dHx_y, dHy_z, dHx_z};   // pair order of axes 0, 1, 2
+                if (kRare && sec) {   // further slab axes, both points at once
 #pragma unroll
-                    for (int p = 0; p < 2; ++p) {
-                        if (!(p ? v1 : v0)) continue;
-#pragma unroll 1
-                        for (int a = 0; a < 3; ++a) {
-                            if (!((sec >> a) & 1u)) continue;
-                            const int pos = a == 0 ? gx0 + p : a == 1 ? gy : k;
-                            if (!slab_pos(P, a, pos)) continue;
-                            const float bb = __ldg(P.pbE[a] + pos), cc = __ldg(P.pcE[a] + pos);
-                            const int c1 = pair_c1(a), c2 = pair_c2(a);
-                            float* w1 = P.psiE[c1][a] + q + p;
-                            float* w2 = P.psiE[c2][a] + q + p;
-                            const float d1 = p ? hi(dh[2 * a]) : lo(dh[2 * a]);
-                            const float d2 = p ? hi(dh[2 * a + 1]) : lo(dh[2 * a + 1]);
-                            const float n1 = bb * *w1 + cc * d1, n2 = bb * *w2 + cc * d2;
-                            // the pair (c1, c2) of axis a enters the curl with signs (-, +), (+, -), (-, +)
-                            const float s = a == 1 ? 1.f : -1.f;
-                            c3[c1][p] += s * n1;
-                            c3[c2][p] -= s * n2;
-                            if (mk >> (6 * p + 3 + c1) & 1u) *w1 = n1;
-                            if (mk >> (6 * p + 3 + c2) & 1u) *w2 = n2;
+                    for (int a = 0; a < 3; ++a) {
+                        if (!((sec >> a) & 1u)) continue;
+                        const int pos0 = a == 0 ? gx0 : a == 1 ? gy : k, pos1 = a == 0 ? gx0 + 1 : pos0;
+                        const bool in0 = v0 && slab_pos(P, a, pos0), in1 = v1 && slab_pos(P, a, pos1);
+                        if (!in0 && !in1) continue;
+                        const f2 bb = pk(in0 ? __ldg(P.pbE[a] + pos0) : 0.f, in1 ? __ldg(P.pbE[a] + pos1) : 0.f);
+                        const f2 cc = pk(in0 ? __ldg(P.pcE[a] + pos0) : 0.f, in1 ? __ldg(P.pcE[a] + pos1) : 0.f);
+                        float* w1 = P.psiE[pair_c1(a)][a] + q;
+                        float* w2 = P.psiE[pair_c2(a)][a] + q;
+                        const f2 d1 = a == 0 ? dHz_x : a == 1 ? dHz_y : dHy_z;
+                        const f2 d2 = a == 0 ? dHy_x : a == 1 ? dHx_y : dHx_z;
+                        const f2 n1 = fma2(bb, ld2g(w1, v1), mul2(cc, d1));
+                        const f2 n2 = fma2(bb, ld2g(w2, v1), mul2(cc, d2));
+                        // the pair of axis a enters the curl with signs (-, +), (+, -), (-, +)
+                        if (a == 0) {
+                            cy = sub2(cy, n1);
+                            cz = add2(cz, n2);
+                        } else if (a == 1) {
+                            cx = add2(cx, n1);
+                            cz = sub2(cz, n2);
+                        } else {
+                            cx = sub2(cx, n1);
+                            cy = add2(cy, n2);
                         }
+                        const unsigned inm = (in0 ? 1u : 0u) | (in1 ? 2u : 0u);
+                        st2m(w1, n1, inm & mbits(mk, 3 + pair_c1(a)));
+                        st2m(w2, n2, inm & mbits(mk, 3 + pair_c2(a)));
                     }
-                    cx = pk(c3[0][0], c3[0][1]);
-                    cy = pk(c3[1][0], c3[1][1]);
-                    cz = pk(c3[2][0], c3[2][1]);
                 }
                 // Js^{n+1/2} = Js + kt E^n, E^{n+1} = ca E^n + cb (curl - Js^{n+1/2})
                 f2 jt0 = 0, jt1 = 0, jt2 = 0;
@@ -831,18 +832,28 @@ __global__ void __launch_bounds__(kThreads, 2)
                 f2 n0 = fma2(cb0, sub2(cx, jt0), mul2(ca0, em0));
                 f2 n1 = fma2(cb1, sub2(cy, jt1), mul2(ca1, em1));
                 f2 n2 = fma2(cb2, sub2(cz, jt2), mul2(ca2, em2));
-                if (kRare && (f & kFSrc)) {   // soft sources, point by point
-                    float e3[3][2] = {{lo(n0), hi(n0)}, {lo(n1), hi(n1)}, {lo(n2), hi(n2)}};
+                if (kRare && (f & kFSrc)) {   // soft sources
+                    float ax0 = 0.f, ax1 = 0.f, ay0 = 0.f, ay1 = 0.f, az0 = 0.f, az1 = 0.f;
                     for (int s = 0; s < S.n; ++s) {
                         if (gy < S.lo[s][1] || gy >= S.hi[s][1] || k < S.lo[s][2] || k >= S.hi[s][2]) continue;
+                        const float v = S.amp[s];
+                        const float u0 = (gx0 >= S.lo[s][0] && gx0 < S.hi[s][0]) ? v : 0.f;
+                        const float u1 = (gx0 + 1 >= S.lo[s][0] && gx0 + 1 < S.hi[s][0]) ? v : 0.f;
                         const int c = S.comp[s];
-#pragma unroll
-                        for (int p = 0; p < 2; ++p)
-                            if (gx0 + p >= S.lo[s][0] && gx0 + p < S.hi[s][0]) e3[c][p] += S.amp[s];
+                        if (c == 0) {
+                            ax0 += u0;
+                            ax1 += u1;
+                        } else if (c == 1) {
+                            ay0 += u0;
+                            ay1 += u1;
+                        } else {
+                            az0 += u0;
+                            az1 += u1;
+                        }
                     }
-                    n0 = pk(e3[0][0], e3[0][1]);
-                    n1 = pk(e3[1][0], e3[1][1]);
-                    n2 = pk(e3[2][0], e3[2][1]);
+                    n0 = add2(n0, pk(ax0, ax1));
+                    n1 = add2(n1, pk(ay0, ay1));
+                    n2 = add2(n2, pk(az0, az1));
                 }
                 if (masked) {
                     n0 = sel2(n0, em0, mbits(mk, 3));
