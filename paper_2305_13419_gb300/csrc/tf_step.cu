@@ -641,27 +641,46 @@ __global__ void __launch_bounds__(kThreads, 2)
             // ------------------------------------------------ B phase
             f2 p0, p1;
             P3 nb = b_pair(P, s0, s1, j, i0, sax, bB, cB, p0, p1);
-            if (kRare && sec) {   // CPML memory of further slab axes, point by point
-                V3 b[2] = {{lo(nb.x), lo(nb.y), lo(nb.z)}, {hi(nb.x), hi(nb.y), hi(nb.z)}};
+            if (kRare && sec) {   // CPML memory of further slab axes, both points at once
 #pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    if (!(p ? v1 : v0)) continue;
-#pragma unroll 1
-                    for (int a = 0; a < 3; ++a) {
-                        if (!((sec >> a) & 1u)) continue;
-                        const int pos = a == 0 ? gx0 + p : a == 1 ? gy : k;
-                        if (!slab_pos(P, a, pos)) continue;
-                        float e0, e1;
-                        b_psi_extra(P, s0, s1, j, i0 + p, a, pos, q + p, b[p], e0, e1);
-                        if (own) {
-                            if (mk >> (6 * p + pair_c1(a)) & 1u) O.psiB[pair_c1(a)][a][q + p] = e0;
-                            if (mk >> (6 * p + pair_c2(a)) & 1u) O.psiB[pair_c2(a)][a][q + p] = e1;
-                        }
+                for (int a = 0; a < 3; ++a) {
+                    if (!((sec >> a) & 1u)) continue;
+                    const int pos0 = a == 0 ? gx0 : a == 1 ? gy : k, pos1 = a == 0 ? gx0 + 1 : pos0;
+                    const bool in0 = v0 && slab_pos(P, a, pos0), in1 = v1 && slab_pos(P, a, pos1);
+                    if (!in0 && !in1) continue;
+                    const f2 bb = pk(in0 ? __ldg(P.pbB[a] + pos0) : 0.f, in1 ? __ldg(P.pbB[a] + pos1) : 0.f);
+                    const f2 cc = pk(in0 ? __ldg(P.pcB[a] + pos0) : 0.f, in1 ? __ldg(P.pcB[a] + pos1) : 0.f);
+                    // differences of E along a feeding the pair (c1, c2) of axis a
+                    f2 d0, d1;
+                    if (a == 0) {
+                        const f2 ez = ld2(&s0.e[2][j][i0]), ey = ld2(&s0.e[1][j][i0]);
+                        d0 = sub2(pk(hi(ez), s0.e[2][j][i0 + 2]), ez);
+                        d1 = sub2(pk(hi(ey), s0.e[1][j][i0 + 2]), ey);
+                    } else if (a == 1) {
+                        d0 = sub2(ld2(&s0.e[2][j + 1][i0]), ld2(&s0.e[2][j][i0]));
+                        d1 = sub2(ld2(&s0.e[0][j + 1][i0]), ld2(&s0.e[0][j][i0]));
+                    } else {
+                        d0 = sub2(ld2(&s1.e[1][j][i0]), ld2(&s0.e[1][j][i0]));
+                        d1 = sub2(ld2(&s1.e[0][j][i0]), ld2(&s0.e[0][j][i0]));
+                    }
+                    const f2 n0 = fma2(bb, ld2g(P.psiB[pair_c1(a)][a] + q, v1), mul2(cc, d0));
+                    const f2 n1 = fma2(bb, ld2g(P.psiB[pair_c2(a)][a] + q, v1), mul2(cc, d1));
+                    if (a == 0) {
+                        nb.y = add2(nb.y, n0);
+                        nb.z = sub2(nb.z, n1);
+                    } else if (a == 1) {
+                        nb.x = sub2(nb.x, n0);
+                        nb.z = add2(nb.z, n1);
+                    } else {
+                        nb.x = add2(nb.x, n0);
+                        nb.y = sub2(nb.y, n1);
+                    }
+                    if (own) {
+                        const unsigned inm = (in0 ? 1u : 0u) | (in1 ? 2u : 0u);
+                        st2m(O.psiB[pair_c1(a)][a] + q, n0, inm & mbits(mk, pair_c1(a)));
+                        st2m(O.psiB[pair_c2(a)][a] + q, n1, inm & mbits(mk, pair_c2(a)));
                     }
                 }
-                nb.x = pk(b[0].x, b[1].x);
-                nb.y = pk(b[0].y, b[1].y);
-                nb.z = pk(b[0].z, b[1].z);
             }
             if (masked) {
                 nb.x = sel2(nb.x, ld2(&s0.b[0][j][i0]), mbits(mk, 0));
