@@ -473,11 +473,11 @@ def run_all_configs(args):
     from paper_2305_13419_gb300 import workloads as W
     out = {}
     slab = W.slab()
-    out["1_slab"] = {"gpu": run_config(slab, 4000, 50), "cpu_oracle": cpu_baseline(slab, budget_s=5.0)}
+    out["slab-4x4x2048"] = {"gpu": run_config(slab, 4000, 50), "cpu_oracle": cpu_baseline(slab, budget_s=5.0)}
     cpw = W.cpw()
-    out["2_cpw"] = {"gpu": run_config(cpw, 2000, 20), "cpu_oracle": cpu_baseline(cpw, budget_s=10.0)}
-    plain = out["2_cpw"]["gpu"]["gcell_updates_per_s"]
-    out["3_batch"] = {"gpu": run_batch(args, plain),
+    out["cpw-512x256x128"] = {"gpu": run_config(cpw, 2000, 20), "cpu_oracle": cpu_baseline(cpw, budget_s=10.0)}
+    plain = out["cpw-512x256x128"]["gpu"]["gcell_updates_per_s"]
+    out["batch-64-cpw"] = {"gpu": run_batch(args, plain),
                       "cpu_oracle": cpu_baseline(W.cpw_batch(count=1, sizes=(128,))[0], budget_s=10.0)}
     adj_w = W.cpw_adjoint()
     cpu_adj = cpu_baseline(adj_w, budget_s=10.0)
@@ -488,14 +488,14 @@ def run_all_configs(args):
     g.adjoint_run(16, pr.comp, pr.p, float(pr.freqs[0]), 0)
     el = time.perf_counter() - t0
     cpu_adj["adjoint_forward_plus_backward_gcell_updates_per_s"] = adj_w.ncells * 16 / el / 1e9
-    out["4_adjoint"] = {"gpu": run_adjoint(args), "cpu_oracle": cpu_adj}
+    out["adjoint-cpw-256x128x64"] = {"gpu": run_adjoint(args), "cpu_oracle": cpu_adj}
     large = W.cpw_large()
     sl = (slice(0, 128), slice(128, 384), slice(256, 512))
     block = W.Workload(name="cpw-1024x512x256[256:512,128:384,0:128]", n=(256, 256, 128), d=large.d,
                        theta=large.theta, bc=("pec", "pec", "pec"), eps_r=np.ascontiguousarray(large.eps_r[sl]),
                        mu_r=np.ascontiguousarray(large.mu_r[sl]), lambda_L=np.ascontiguousarray(large.lambda_L[sl]),
                        sigma=np.ascontiguousarray(large.sigma[sl]), courant=large.courant)
-    out["5_large"] = {"gpu": run_config(large, args.large_steps, 5), "cpu_oracle": cpu_baseline(block, budget_s=10.0)}
+    out["cpw-1024x512x256"] = {"gpu": run_config(large, args.large_steps, 5), "cpu_oracle": cpu_baseline(block, budget_s=10.0)}
     print(json.dumps({"all_configs": out}), flush=True)
     return 0
 

@@ -58,7 +58,7 @@ typedef enum {
     TF_ESTATE = 5,      /* call not allowed in the handle's current state */
     TF_ETIMEOUT = 6,    /* a bounded device wait gave up */
     TF_ENONFINITE = 7,  /* the watchdog saw a non-finite E value */
-    TF_ENOTSUP = 8      /* valid request this build does not support */
+    TF_ENOTSUP = 8      /* valid request the library does not support */
 } tf_status;
 
 /* boundary kinds (Sec. 3: periodic, PEC and PML; Mur offered for quasi-1-D runs) */

@@ -1,6 +1,6 @@
 """Compile the C oracle into oracle/lib/libtwofluid_oracle.so (gcc, OpenMP).
 
-TEST INFRASTRUCTURE: the checker is built, never used, by the product path.
+TEST INFRASTRUCTURE: built alongside the library, never used by the product path.
 Flags: -O2, no fast-math and no FMA contraction, so the oracle rounds the
 same way on x86-64 and aarch64.
 """

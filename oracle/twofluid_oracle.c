@@ -20,7 +20,7 @@
  *     4. Js^{n+1}   = Js^{n+1/2} + dt/2 E^{n+1} / (lambda^2 mu)  (SC edges)
  *     5. B^{n+1}    = B^{n+1/2} - dt/2 curl E^{n+1}
  *
- * Readings of points the paper leaves open (each listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - edge material (Sec. 3: edges on an interface count as superconducting;
  *     sharp jumps in sigma or 1/lambda make the scheme first order in space,
  *     smooth ones keep second order): an edge takes the arithmetic mean of eps

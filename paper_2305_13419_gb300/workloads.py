@@ -300,7 +300,7 @@ def cpw_small(seed: int = BASE_SEED + 12, nsteps: int = 1200, **kw) -> Workload:
 
 def cpw_large(nsteps: int = 50000, **kw) -> Workload:
     """1024 x 512 x 256 CPW (134 M cells), lambda_L = 4 cells, CPML 16; the
-    config-2 template with every transverse feature doubled."""
+    512 x 256 x 128 CPW template with every transverse feature doubled."""
     args = dict(n=(1024, 512, 256), pml=16, margin=4, substrate_cells=64, film_cells=8,
                 strip_w=32, gap_w=16, lam_cells=4.0, nsteps=nsteps, seed=BASE_SEED + 5)
     args.update(kw)
@@ -308,7 +308,7 @@ def cpw_large(nsteps: int = 50000, **kw) -> Workload:
 
 
 def cpw_adjoint(nsteps: int = 8000, seed: int = BASE_SEED + 4, **kw) -> Workload:
-    """The adjoint workload: a 256 x 128 x 64 CPW (the config-2 template at
+    """The adjoint workload: a 256 x 128 x 64 CPW (the 512 x 256 x 128 template at
     half size: CPML 12, 16-cell substrate, 2-cell films, 8-wide strip) whose
     substrate eps_r is drawn per cell from U[10, 13]; the objective is |X|^2
     of probe 0's DFT at the template's resonance estimate f0 (frequency
@@ -330,7 +330,7 @@ def cpw_adjoint(nsteps: int = 8000, seed: int = BASE_SEED + 4, **kw) -> Workload
 
 def cpw_batch(count: int = 64, seed: int = BASE_SEED + 3, nsteps: int = 8000, sizes=(96, 128, 160)):
     """The batched workload: `count` CPW resonator variants, each axis drawn
-    independently from `sizes`; the config-2 template scaled to each grid
+    independently from `sizes`; the 512 x 256 x 128 CPW template scaled to each grid
     (CPML, margin, substrate and film thickness in proportion to the axis),
     strip and gap widths drawn from U{4..16}, lambda_L from U[2, 6] cells and
     sigma_n per metal cell from U[0, 1e6] S/m."""
@@ -375,5 +375,5 @@ def random_box(n=(9, 7, 11), bc=("periodic", "periodic", "periodic"), seed: int 
 
 
 def all_configs():
-    """Named workloads: slab (config 1), CPW (2), large CPW (5)."""
+    """Named workloads: the 4 x 4 x 2048 slab, the 512 x 256 x 128 CPW and the 1024 x 512 x 256 CPW."""
     return {"slab": slab, "cpw": cpw, "cpw_small": cpw_small, "cpw_large": cpw_large}

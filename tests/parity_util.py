@@ -12,7 +12,7 @@ import numpy as np
 from oracle import stepper
 from paper_2305_13419_gb300 import workloads as W
 
-FIELD_TOL = 1e-4   # relative L2 on fields after the stated steps (spec tolerance)
+FIELD_TOL = 1e-4   # relative L2 on fields after the stated steps
 SPEC_TOL = 1e-3    # relative on probe spectra and Q
 
 

@@ -83,7 +83,7 @@ def test_probe_series_and_wall_probe():
         assert np.max(np.abs(sg - so)) <= 1e-4 * max(np.max(np.abs(so)), 1e-30) + 1e-12
 
 
-# ----------------------------------------------------------- config 1: slab
+# ----------------------------------------------------------- 4 x 4 x 2048 slab
 @pytest.mark.parametrize("boundary", ["mur", "cpml"])
 def test_slab_config(boundary):
     """4 x 4 x 2048 slab, 4000 steps: fields, and the probe spectra at the
@@ -98,7 +98,7 @@ def test_slab_config(boundary):
         assert rel_l2(Xg, Xo) < SPEC_TOL, p
 
 
-# ----------------------------------------------------------- config 2 (scaled)
+# ----------------------------------------------------------- CPW resonator (scaled)
 def test_cpw_small_fields_spectra_q():
     """Scaled CPW resonator, 3000 steps: fields near their peak (raw relative
     L2), fields at the end of the ring-down (relative to the peak norm of the

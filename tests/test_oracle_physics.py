@@ -173,7 +173,7 @@ def test_cube_time_second_order():
 
 # ---------------------------------------------- decay inside the superconductor
 def test_slab_decay_matches_discrete_and_continuum():
-    """Config-1 slab (lambda = 8 cells, sigma = 0): the ratio of probe DFTs
+    """4 x 4 x 2048 slab (lambda = 8 cells, sigma = 0): the ratio of probe DFTs
     8 cells apart inside the superconductor equals exp(-8 kd d), kd from the
     scheme's evanescent dispersion (to 1 %), and tracks the continuum skin
     depth of Eq. skin to O((d/lambda)^2)."""
