@@ -64,7 +64,7 @@ Layout layout_of(const tf_grid_desc* d) {
     Layout L{};
     const int n[3] = {d->nx, d->ny, d->nz};
     for (int a = 0; a < 3; ++a) L.N[a] = n[a] + (d->bc[a].kind == TF_BC_PERIODIC ? 0 : 1);
-    L.pitch = (L.N[0] + 31) / 32 * 32;
+    L.pitch = (L.N[0] + 1 + 31) / 32 * 32;   // a spare column past the x end
     L.total = (long long)L.pitch * L.N[1] * L.N[2];
     L.ncell = (long long)n[0] * n[1] * n[2];
     L.ndense = (long long)L.N[0] * L.N[1] * L.N[2];

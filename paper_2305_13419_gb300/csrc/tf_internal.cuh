@@ -38,7 +38,7 @@ struct Params {
     int per[3];          // periodic flag per axis
     int bc[3];           // TF_BC_* per axis
     int L[3];            // CPML cells per axis (0 without CPML)
-    int pitch;           // floats per x row (multiple of 32)
+    int pitch;           // floats per x row (multiple of 32, at least N[0] + 1)
     long long plane;     // floats per z plane
     float r[3];          // c0 dt / d_a
     float theta;

@@ -206,17 +206,11 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
-// 8-byte aligned pair in shared or global memory
+// 8-byte aligned pair in shared or global memory.  A global pair whose high
+// point lies past the grid's x end reads and writes the spare column every
+// row has there (the row pitch is at least N0 + 1); nothing reads it back.
 __device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
 __device__ __forceinline__ void st2(float* p, f2 v) { *reinterpret_cast<f2*>(p) = v; }
-// global pair whose high point may lie past the grid's x end (then read as 0 / not written)
-__device__ __forceinline__ f2 ld2g(const float* p, bool both) { return both ? ld2(p) : pk(p[0], 0.f); }
-__device__ __forceinline__ void st2g(float* p, f2 v, bool both) {
-    if (both)
-        st2(p, v);
-    else
-        p[0] = lo(v);
-}
 // store the points whose bit is set in m (bit 0: low, bit 1: high)
 __device__ __forceinline__ void st2m(float* p, f2 v, unsigned m) {
     if (m == 3u)
@@ -546,21 +540,21 @@ __global__ void __launch_bounds__(kThreads, 2)
             // global reads that do not depend on the stage: issued before the wait
             f2 jo0 = 0, jo1 = 0, jo2 = 0;
             if (own && sc) {
-                jo0 = ld2g(P.J[0] + q, v1);
-                jo1 = ld2g(P.J[1] + q, v1);
-                jo2 = ld2g(P.J[2] + q, v1);
+                jo0 = ld2(P.J[0] + q);
+                jo1 = ld2(P.J[1] + q);
+                jo2 = ld2(P.J[2] + q);
             }
             f2 ca0, ca1, ca2, cb0, cb1, cb2, cj0, cj1, cj2;
             if (own && coef) {
-                ca0 = ld2g(P.ca[0] + q, v1);
-                ca1 = ld2g(P.ca[1] + q, v1);
-                ca2 = ld2g(P.ca[2] + q, v1);
-                cb0 = ld2g(P.cb[0] + q, v1);
-                cb1 = ld2g(P.cb[1] + q, v1);
-                cb2 = ld2g(P.cb[2] + q, v1);
-                cj0 = ld2g(P.cj[0] + q, v1);
-                cj1 = ld2g(P.cj[1] + q, v1);
-                cj2 = ld2g(P.cj[2] + q, v1);
+                ca0 = ld2(P.ca[0] + q);
+                ca1 = ld2(P.ca[1] + q);
+                ca2 = ld2(P.ca[2] + q);
+                cb0 = ld2(P.cb[0] + q);
+                cb1 = ld2(P.cb[1] + q);
+                cb2 = ld2(P.cb[2] + q);
+                cj0 = ld2(P.cj[0] + q);
+                cj1 = ld2(P.cj[1] + q);
+                cj2 = ld2(P.cj[2] + q);
             } else {
                 ca0 = ca1 = ca2 = pk(rec.x, rec.x);
                 cb0 = cb1 = cb2 = pk(rec.y, rec.y);
@@ -591,8 +585,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                 bE = pk(c0, c1);
                 cE = pk(d0, d1);
                 if (own && sl) {
-                    pe0 = ld2g(P.psiE[pair_c1(sax)][sax] + q, v1);
-                    pe1 = ld2g(P.psiE[pair_c2(sax)][sax] + q, v1);
+                    pe0 = ld2(P.psiE[pair_c1(sax)][sax] + q);
+                    pe1 = ld2(P.psiE[pair_c2(sax)][sax] + q);
                 }
                 if (hal) {
                     const int hp0 = sax == 0 ? hgx0 : sax == 1 ? hgy : k, hp1 = sax == 0 ? hgx0 + 1 : hp0;
@@ -663,8 +657,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                         d0 = sub2(ld2(&s1.e[1][j][i0]), ld2(&s0.e[1][j][i0]));
                         d1 = sub2(ld2(&s1.e[0][j][i0]), ld2(&s0.e[0][j][i0]));
                     }
-                    const f2 n0 = fma2(bb, ld2g(P.psiB[pair_c1(a)][a] + q, v1), mul2(cc, d0));
-                    const f2 n1 = fma2(bb, ld2g(P.psiB[pair_c2(a)][a] + q, v1), mul2(cc, d1));
+                    const f2 n0 = fma2(bb, ld2(P.psiB[pair_c1(a)][a] + q), mul2(cc, d0));
+                    const f2 n1 = fma2(bb, ld2(P.psiB[pair_c2(a)][a] + q), mul2(cc, d1));
                     if (a == 0) {
                         nb.y = add2(nb.y, n0);
                         nb.z = sub2(nb.z, n1);
@@ -691,9 +685,9 @@ __global__ void __launch_bounds__(kThreads, 2)
             st2(&bn[1][j][i0], nb.y);
             st2(&bn[2][j][i0], nb.z);
             if (own) {
-                st2g(O.B[0] + q, nb.x, v1);
-                st2g(O.B[1] + q, nb.y, v1);
-                st2g(O.B[2] + q, nb.z, v1);
+                st2(O.B[0] + q, nb.x);
+                st2(O.B[1] + q, nb.y);
+                st2(O.B[2] + q, nb.z);
                 if (sl) {
                     const unsigned vm = v1 ? 3u : 1u;
                     st2m(O.psiB[pair_c1(sax)][sax] + q, p0, sl & vm & mbits(mk, pair_c1(sax)));
@@ -823,8 +817,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                         float* w2 = P.psiE[pair_c2(a)][a] + q;
                         const f2 d1 = a == 0 ? dHz_x : a == 1 ? dHz_y : dHy_z;
                         const f2 d2 = a == 0 ? dHy_x : a == 1 ? dHx_y : dHx_z;
-                        const f2 n1 = fma2(bb, ld2g(w1, v1), mul2(cc, d1));
-                        const f2 n2 = fma2(bb, ld2g(w2, v1), mul2(cc, d2));
+                        const f2 n1 = fma2(bb, ld2(w1), mul2(cc, d1));
+                        const f2 n2 = fma2(bb, ld2(w2), mul2(cc, d2));
                         // the pair of axis a enters the curl with signs (-, +), (+, -), (-, +)
                         if (a == 0) {
                             cy = sub2(cy, n1);
@@ -882,13 +876,13 @@ __global__ void __launch_bounds__(kThreads, 2)
                     jt1 = sel2(jt1, jo1, mbits(mk, 4));
                     jt2 = sel2(jt2, jo2, mbits(mk, 5));
                 }
-                st2g(O.E[0] + q, n0, v1);
-                st2g(O.E[1] + q, n1, v1);
-                st2g(O.E[2] + q, n2, v1);
+                st2(O.E[0] + q, n0);
+                st2(O.E[1] + q, n1);
+                st2(O.E[2] + q, n2);
                 if (sc) {
-                    st2g(P.J[0] + q, jt0, v1);
-                    st2g(P.J[1] + q, jt1, v1);
-                    st2g(P.J[2] + q, jt2, v1);
+                    st2(P.J[0] + q, jt0);
+                    st2(P.J[1] + q, jt1);
+                    st2(P.J[2] + q, jt2);
                 }
                 if (sl) {
                     const unsigned vm = v1 ? 3u : 1u;
