@@ -249,10 +249,10 @@ __device__ __forceinline__ unsigned masks_of(const Params& P, int gx0, int gy) {
 constexpr unsigned kMaskZlo = (1u << 2 | 1u << 3 | 1u << 4) * 65u;
 // the two point bits (low, high) of mask bit `b`
 __device__ __forceinline__ unsigned mbits(unsigned m, int b) { return (m >> b & 1u) | (m >> (b + 5) & 2u); }
-// per point: m bit set -> new value, else old value
+// per point: m bit set -> new value, else old value (a bitwise select, no branch)
 __device__ __forceinline__ f2 sel2(f2 nv, f2 ov, unsigned m2) {
-    if (m2 == 3u) return nv;
-    return pk((m2 & 1u) ? lo(nv) : lo(ov), (m2 & 2u) ? hi(nv) : hi(ov));
+    const f2 M = (f2)(0u - (m2 & 1u)) | (f2)(0u - (m2 >> 1 & 1u)) << 32;
+    return (nv & M) | (ov & ~M);
 }
 
 // B^{n+1/2} before masking at the pair of box positions (j, i0), (j, i0 + 1)
