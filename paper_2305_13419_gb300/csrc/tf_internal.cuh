@@ -73,6 +73,9 @@ constexpr int kEX = kTX + 8, kEY = kTY + 2;  // E box: x0-4 .. x0+35, y0-1 .. y0
 constexpr int kBX = kTX + 4, kBY = kTY + 1;  // B / psi_B box: x0-4 .. x0+31, y0-1 .. y0+kTY-1
 constexpr int kStages = 4;                   // planes in flight per CTA
 constexpr int kChunk = 8;                    // z planes per work item
+// per-item CPML coefficient table: kBX columns, kBY rows, kChunk + 2 planes per profile
+constexpr int kCfY = kBX, kCfZ = kBX + kBY, kCfN = 64;
+static_assert(kCfZ + kChunk + 2 <= kCfN && 4 * kCfN <= kTX * (kTY / kRows), "one table entry per thread");
 constexpr int kSub = 2;                      // planes per piece of a work item that takes the full loop
 // a work item is a descriptor: tile (bits 0-15), first plane (16-27), planes - 1 (28-31)
 constexpr int kMaxTiles = 1 << 16, kMaxPlanes = 1 << 12;

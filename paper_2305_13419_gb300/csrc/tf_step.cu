@@ -295,7 +295,7 @@ __device__ __forceinline__ P3 b_pair(const Params& P, const StageBuf& s0, const 
 // CPML memory of a further slab axis a at box position (j, i): old values from
 // global memory (psi index q), new values added to B and returned
 __device__ __forceinline__ void b_psi_extra(const Params& P, const StageBuf& s0, const StageBuf& s1, int j, int i,
-                                            int a, int pos, int q, V3& b, float& p0, float& p1) {
+                                            int a, float bb, float cc, int q, V3& b, float& p0, float& p1) {
     float d0, d1;
     if (a == 0) {
         d0 = s0.e[2][j][i + 1] - s0.e[2][j][i];
@@ -307,7 +307,6 @@ __device__ __forceinline__ void b_psi_extra(const Params& P, const StageBuf& s0,
         d0 = s1.e[1][j][i] - s0.e[1][j][i];
         d1 = s1.e[0][j][i] - s0.e[0][j][i];
     }
-    const float bb = __ldg(P.pbB[a] + pos), cc = __ldg(P.pcB[a] + pos);
     p0 = bb * __ldg(P.psiB[pair_c1(a)][a] + q) + cc * d0;
     p1 = bb * __ldg(P.psiB[pair_c2(a)][a] + q) + cc * d1;
     if (a == 0) {
@@ -361,6 +360,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ int s_item[2];                   // current and next work item (-1: none)
     __shared__ float4 s_rec[2][kChunk + 2];     // material record of each plane of the two items
     __shared__ unsigned s_flag[2][kChunk + 2];  // plane flags
+    // CPML coefficients of the two items (zero outside the slabs): per profile
+    // (b_B, c_B, b_E, c_E) the tile's columns x0-4 .. x0+31, rows y0-1 ..
+    // y0+15 and the item's planes
+    __shared__ __align__(16) float s_cf[2][4][kCfN];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
     const int nitems = O.nitems;
     const int PL = (int)P.plane;
@@ -371,14 +374,33 @@ __global__ void __launch_bounds__(kThreads, 2)
         return (d >= 0 && d < nitems) ? __ldg(O.order + d) : -1;
     };
     // the records of an item: loaded by threads < nq - 1 ...
-    auto rec_load = [&](int item, float4& r) {
+    auto rec_load = [&](int item, float4& r, float& cf) {
         if (item < 0) return;
         const Tile t = tile_of(P, O, item);
         if (tid < t.nq - 1) r = __ldg(O.tilemat + (long long)(t.by * O.ntx + t.bx) * P.N[2] + plane_of(P, t, tid));
+        // one coefficient table entry per thread: profile tid / kCfN, entry tid % kCfN
+        const int pr = tid / kCfN, e = tid % kCfN;
+        int a = -1, pos = 0;
+        if (e < kCfY) {
+            a = 0;
+            pos = t.x0 - 4 + e;
+        } else if (e < kCfZ) {
+            a = 1;
+            pos = t.y0 - 1 + (e - kCfY);
+        } else if (e - kCfZ < t.nq - 1) {
+            a = 2;
+            pos = plane_of(P, t, e - kCfZ);
+        }
+        cf = 0.f;
+        if (a >= 0 && slab_pos(P, a, pos)) {
+            const float* pf = pr == 0 ? P.pbB[a] : pr == 1 ? P.pcB[a] : pr == 2 ? P.pbE[a] : P.pcE[a];
+            cf = __ldg(pf + pos);
+        }
     };
     // ... and stored with the plane flags
-    auto rec_store = [&](int item, int slot, const float4& r) {
+    auto rec_store = [&](int item, int slot, const float4& r, float cf) {
         if (item < 0) return;
+        (&s_cf[slot][0][0])[tid] = cf;
         const Tile t = tile_of(P, O, item);
         if (tid < t.nq - 1) {
             const int k = plane_of(P, t, tid);
@@ -454,10 +476,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     {
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
-        rec_load(s_item[0], r0);
-        rec_load(s_item[1], r1);
-        rec_store(s_item[0], 0, r0);
-        rec_store(s_item[1], 1, r1);
+        float f0 = 0.f, f1 = 0.f;
+        rec_load(s_item[0], r0, f0);
+        rec_load(s_item[1], r1, f1);
+        rec_store(s_item[0], 0, r0, f0);
+        rec_store(s_item[1], 1, r1, f1);
     }
     if (tid == kProd) pump();
     __syncthreads();
@@ -514,6 +537,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
         };
         float4 rnext = make_float4(0.f, 0.f, 0.f, 0.f);   // records of the next item
+        float cfnext = 0.f;                                 // and this thread's coefficient entry
         f2 bpx = 0, bpy = 0;     // B^{n+1/2}(k-1) at the own pair (z differences)
         f2 elo0 = 0, elo1 = 0;   // E^n on the low Mur wall
         // one plane, compiled twice: items that meet a source, a Mur plane, a
@@ -565,42 +589,33 @@ __global__ void __launch_bounds__(kThreads, 2)
             unsigned sl = 0;   // bit p: point p inside the slab
             if (sax >= 0) {
                 const int pos0 = sax == 0 ? gx0 : sax == 1 ? gy : k, pos1 = sax == 0 ? gx0 + 1 : pos0;
-                float a0 = 0.f, b0 = 0.f, c0 = 0.f, d0 = 0.f, a1 = 0.f, b1 = 0.f, c1 = 0.f, d1 = 0.f;
-                if (slab_pos(P, sax, pos0)) {
-                    sl |= 1u;
-                    a0 = __ldg(P.pbB[sax] + pos0);
-                    b0 = __ldg(P.pcB[sax] + pos0);
-                    c0 = __ldg(P.pbE[sax] + pos0);
-                    d0 = __ldg(P.pcE[sax] + pos0);
+                sl = (slab_pos(P, sax, pos0) ? 1u : 0u) | (slab_pos(P, sax, pos1) ? 2u : 0u);
+                const float(*cf)[kCfN] = s_cf[cur];
+                if (sax == 0) {
+                    bB = ld2(&cf[0][i0]);
+                    cB = ld2(&cf[1][i0]);
+                    bE = ld2(&cf[2][i0]);
+                    cE = ld2(&cf[3][i0]);
+                } else {
+                    const int e = sax == 1 ? kCfY + j : kCfZ + qq;
+                    bB = pk(cf[0][e], cf[0][e]);
+                    cB = pk(cf[1][e], cf[1][e]);
+                    bE = pk(cf[2][e], cf[2][e]);
+                    cE = pk(cf[3][e], cf[3][e]);
                 }
-                if (slab_pos(P, sax, pos1)) {
-                    sl |= 2u;
-                    a1 = __ldg(P.pbB[sax] + pos1);
-                    b1 = __ldg(P.pcB[sax] + pos1);
-                    c1 = __ldg(P.pbE[sax] + pos1);
-                    d1 = __ldg(P.pcE[sax] + pos1);
-                }
-                bB = pk(a0, a1);
-                cB = pk(b0, b1);
-                bE = pk(c0, c1);
-                cE = pk(d0, d1);
                 if (own && sl) {
                     pe0 = ld2(P.psiE[pair_c1(sax)][sax] + q);
                     pe1 = ld2(P.psiE[pair_c2(sax)][sax] + q);
                 }
                 if (hal) {
-                    const int hp0 = sax == 0 ? hgx0 : sax == 1 ? hgy : k, hp1 = sax == 0 ? hgx0 + 1 : hp0;
-                    float e0 = 0.f, e1 = 0.f, h0 = 0.f, h1 = 0.f;
-                    if (slab_pos(P, sax, hp0)) {
-                        e0 = __ldg(P.pbB[sax] + hp0);
-                        h0 = __ldg(P.pcB[sax] + hp0);
+                    if (sax == 0) {
+                        hbB = ld2(&cf[0][hi0]);
+                        hcB = ld2(&cf[1][hi0]);
+                    } else {
+                        const int e = sax == 1 ? kCfY + hj : kCfZ + qq;
+                        hbB = pk(cf[0][e], cf[0][e]);
+                        hcB = pk(cf[1][e], cf[1][e]);
                     }
-                    if (slab_pos(P, sax, hp1)) {
-                        e1 = __ldg(P.pbB[sax] + hp1);
-                        h1 = __ldg(P.pcB[sax] + hp1);
-                    }
-                    hbB = pk(e0, e1);
-                    hcB = pk(h0, h1);
                 }
             }
             if (kRare && sec) {   // CPML memories of the further slab axes: into L1 while the stage lands
@@ -642,8 +657,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                     const int pos0 = a == 0 ? gx0 : a == 1 ? gy : k, pos1 = a == 0 ? gx0 + 1 : pos0;
                     const bool in0 = v0 && slab_pos(P, a, pos0), in1 = v1 && slab_pos(P, a, pos1);
                     if (!in0 && !in1) continue;
-                    const f2 bb = pk(in0 ? __ldg(P.pbB[a] + pos0) : 0.f, in1 ? __ldg(P.pbB[a] + pos1) : 0.f);
-                    const f2 cc = pk(in0 ? __ldg(P.pcB[a] + pos0) : 0.f, in1 ? __ldg(P.pcB[a] + pos1) : 0.f);
+                    const int e0 = a == 0 ? i0 : a == 1 ? kCfY + j : kCfZ + qq, e1 = a == 0 ? i0 + 1 : e0;
+                    const f2 bb = pk(in0 ? s_cf[cur][0][e0] : 0.f, in1 ? s_cf[cur][0][e1] : 0.f);
+                    const f2 cc = pk(in0 ? s_cf[cur][1][e0] : 0.f, in1 ? s_cf[cur][1][e1] : 0.f);
                     // differences of E along a feeding the pair (c1, c2) of axis a
                     f2 d0, d1;
                     if (a == 0) {
@@ -708,8 +724,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                             if (!((sec >> a) & 1u)) continue;
                             const int pos = a == 0 ? xw : a == 1 ? yw : k;
                             float e0, e1;   // new halo memory: formed by the owner
+                            const int e = a == 0 ? hi0 + p : a == 1 ? kCfY + hj : kCfZ + qq;
                             if (slab_pos(P, a, pos))
-                                b_psi_extra(P, s0, s1, hj, hi0 + p, a, pos, kq + yw * P.pitch + xw, b[p], e0, e1);
+                                b_psi_extra(P, s0, s1, hj, hi0 + p, a, s_cf[cur][0][e], s_cf[cur][1][e],
+                                            kq + yw * P.pitch + xw, b[p], e0, e1);
                         }
                     }
                     h.x = pk(b[0].x, b[1].x);
@@ -727,7 +745,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     st2(&bn[1][hj][hi0], h.y);
                 st2(&bn[2][hj][hi0], h.z);
             }
-            if (qq == 1) rec_store(s_item[cur ^ 1], cur ^ 1, rnext);   // loaded during plane 0
+            if (qq == 1) rec_store(s_item[cur ^ 1], cur ^ 1, rnext, cfnext);   // loaded during plane 0
             // every thread is past the E phase of the plane before: its stage is free
             if (__syncthreads_or(!ok)) return false;
             if (tid == kProd) {
@@ -735,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 pump();
                 if (qq == 0) pend = s_item[cur ^ 1] >= 0 ? fetch() : -1;
             }
-            if (qq == 0) rec_load(s_item[cur ^ 1], rnext);
+            if (qq == 0) rec_load(s_item[cur ^ 1], rnext, cfnext);
 
             // ------------------------------------------------ E phase
             if (own) {
@@ -811,8 +829,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                         const int pos0 = a == 0 ? gx0 : a == 1 ? gy : k, pos1 = a == 0 ? gx0 + 1 : pos0;
                         const bool in0 = v0 && slab_pos(P, a, pos0), in1 = v1 && slab_pos(P, a, pos1);
                         if (!in0 && !in1) continue;
-                        const f2 bb = pk(in0 ? __ldg(P.pbE[a] + pos0) : 0.f, in1 ? __ldg(P.pbE[a] + pos1) : 0.f);
-                        const f2 cc = pk(in0 ? __ldg(P.pcE[a] + pos0) : 0.f, in1 ? __ldg(P.pcE[a] + pos1) : 0.f);
+                        const int e0 = a == 0 ? i0 : a == 1 ? kCfY + j : kCfZ + qq, e1 = a == 0 ? i0 + 1 : e0;
+                        const f2 bb = pk(in0 ? s_cf[cur][2][e0] : 0.f, in1 ? s_cf[cur][2][e1] : 0.f);
+                        const f2 cc = pk(in0 ? s_cf[cur][3][e0] : 0.f, in1 ? s_cf[cur][3][e1] : 0.f);
                         float* w1 = P.psiE[pair_c1(a)][a] + q;
                         float* w2 = P.psiE[pair_c2(a)][a] + q;
                         const f2 d1 = a == 0 ? dHz_x : a == 1 ? dHz_y : dHy_z;
@@ -929,7 +948,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (aborted) break;
         seq0 += nq;
         // this item is done: its slot takes the item after the next one
-        if (nq == 2) rec_store(s_item[cur ^ 1], cur ^ 1, rnext);   // a one-plane item: no plane 1
+        if (nq == 2) rec_store(s_item[cur ^ 1], cur ^ 1, rnext, cfnext);   // a one-plane item: no plane 1
         if (tid == kProd) {
             s_item[cur] = pend;
             ++c_ord;
