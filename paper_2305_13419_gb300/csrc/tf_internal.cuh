@@ -73,6 +73,13 @@ constexpr int kEX = kTX + 8, kEY = kTY + 2;  // E box: x0-4 .. x0+35, y0-1 .. y0
 constexpr int kBX = kTX + 4, kBY = kTY + 1;  // B / psi_B box: x0-4 .. x0+31, y0-1 .. y0+kTY-1
 constexpr int kStages = 4;                   // planes in flight per CTA
 constexpr int kChunk = 8;                    // z planes per work item
+// The last plane an item pulls is only ever the upper plane of its last
+// step, so the ring must hold the two planes the next item starts with
+// while that one is still in use: four stages at least.
+static_assert(kStages >= 4, "the ring must reach two planes into the next item");
+// A work-item descriptor keeps len - 1 in bits 28..30 so that it stays
+// non-negative (-1 marks the end of the work).
+static_assert(kChunk <= 8, "descriptors must stay non-negative");
 // per-item CPML coefficient table: kBX columns, kBY rows, kChunk + 2 planes per profile
 constexpr int kCfY = kBX, kCfZ = kBX + kBY, kCfN = 64;
 static_assert(kCfZ + kChunk + 2 <= kCfN && 4 * kCfN <= kTX * (kTY / kRows), "one table entry per thread");

@@ -170,10 +170,6 @@ __device__ __forceinline__ bool slab_pos(const Params& P, int a, int p) {
     return p >= 0 && p < P.N[a] && in_slab(P, a, p);
 }
 
-struct V3 {
-    float x, y, z;
-};
-
 // Two horizontally adjacent points travel together: a 64-bit register holds
 // the pair (low: x, high: x + 1) and the sm_100-family packed FP32 pipe
 // (add / sub / mul / fma .f32x2) updates both at once.
@@ -292,32 +288,32 @@ __device__ __forceinline__ P3 b_pair(const Params& P, const StageBuf& s0, const 
     return b;
 }
 
-// CPML memory of a further slab axis a at box position (j, i): old values from
-// global memory (psi index q), new values added to B and returned
-__device__ __forceinline__ void b_psi_extra(const Params& P, const StageBuf& s0, const StageBuf& s1, int j, int i,
-                                            int a, float bb, float cc, int q, V3& b, float& p0, float& p1) {
-    float d0, d1;
+// differences of E along axis a that feed the CPML pair (c1, c2) of that axis,
+// for the pair of box positions (j, i0), (j, i0 + 1)
+__device__ __forceinline__ void e_diffs2(const StageBuf& s0, const StageBuf& s1, int j, int i0, int a, f2& d0, f2& d1) {
     if (a == 0) {
-        d0 = s0.e[2][j][i + 1] - s0.e[2][j][i];
-        d1 = s0.e[1][j][i + 1] - s0.e[1][j][i];
+        const f2 ez = ld2(&s0.e[2][j][i0]), ey = ld2(&s0.e[1][j][i0]);
+        d0 = sub2(pk(hi(ez), s0.e[2][j][i0 + 2]), ez);
+        d1 = sub2(pk(hi(ey), s0.e[1][j][i0 + 2]), ey);
     } else if (a == 1) {
-        d0 = s0.e[2][j + 1][i] - s0.e[2][j][i];
-        d1 = s0.e[0][j + 1][i] - s0.e[0][j][i];
+        d0 = sub2(ld2(&s0.e[2][j + 1][i0]), ld2(&s0.e[2][j][i0]));
+        d1 = sub2(ld2(&s0.e[0][j + 1][i0]), ld2(&s0.e[0][j][i0]));
     } else {
-        d0 = s1.e[1][j][i] - s0.e[1][j][i];
-        d1 = s1.e[0][j][i] - s0.e[0][j][i];
+        d0 = sub2(ld2(&s1.e[1][j][i0]), ld2(&s0.e[1][j][i0]));
+        d1 = sub2(ld2(&s1.e[0][j][i0]), ld2(&s0.e[0][j][i0]));
     }
-    p0 = bb * __ldg(P.psiB[pair_c1(a)][a] + q) + cc * d0;
-    p1 = bb * __ldg(P.psiB[pair_c2(a)][a] + q) + cc * d1;
+}
+// add the new CPML memory pair (n0, n1) of axis a to B with the curl's signs
+__device__ __forceinline__ void b_add_psi(int a, f2 n0, f2 n1, P3& b) {
     if (a == 0) {
-        b.y += p0;
-        b.z -= p1;
+        b.y = add2(b.y, n0);
+        b.z = sub2(b.z, n1);
     } else if (a == 1) {
-        b.x -= p0;
-        b.z += p1;
+        b.x = sub2(b.x, n0);
+        b.z = add2(b.z, n1);
     } else {
-        b.x += p0;
-        b.y -= p1;
+        b.x = add2(b.x, n0);
+        b.y = sub2(b.y, n1);
     }
 }
 
@@ -618,6 +614,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                     }
                 }
             }
+            f2 ho0 = 0, ho1 = 0, ho2 = 0, ho3 = 0;   // halo: old memories of the first two further axes
+            unsigned hin = 0;                        // halo: bits 2a, 2a + 1: point inside the slab of axis a
             if (kRare && sec) {   // CPML memories of the further slab axes: into L1 while the stage lands
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
@@ -628,13 +626,30 @@ __global__ void __launch_bounds__(kThreads, 2)
                         prefetch_l1(P.psiE[pair_c1(a)][a] + q);
                         prefetch_l1(P.psiE[pair_c2(a)][a] + q);
                     }
-                    if (hal) {
-                        const int xw = wrap_or_out(P, 0, hgx0), yw = wrap_or_out(P, 1, hgy);
-                        if (xw >= 0 && yw >= 0) {
-                            const int qh = kq + yw * P.pitch + xw;
-                            prefetch_l1(P.psiB[pair_c1(a)][a] + qh);
-                            prefetch_l1(P.psiB[pair_c2(a)][a] + qh);
+                }
+                if (hal) {   // halo: old memories of the further axes into registers while the stage lands
+                    const int xw0 = wrap_or_out(P, 0, hgx0), xw1 = wrap_or_out(P, 0, hgx0 + 1);
+                    const int yw = wrap_or_out(P, 1, hgy);
+                    const int qh = kq + (yw >= 0 ? yw : 0) * P.pitch;
+                    int n = 0;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        if (!((sec >> a) & 1u)) continue;
+                        const bool in0 = yw >= 0 && xw0 >= 0 && slab_pos(P, a, a == 0 ? xw0 : a == 1 ? yw : k);
+                        const bool in1 = yw >= 0 && xw1 >= 0 && slab_pos(P, a, a == 0 ? xw1 : a == 1 ? yw : k);
+                        hin |= ((in0 ? 1u : 0u) | (in1 ? 2u : 0u)) << (2 * a);
+                        const float* w1 = P.psiB[pair_c1(a)][a];
+                        const float* w2 = P.psiB[pair_c2(a)][a];
+                        const f2 o1 = pk(in0 ? w1[qh + xw0] : 0.f, in1 ? w1[qh + xw1] : 0.f);
+                        const f2 o2 = pk(in0 ? w2[qh + xw0] : 0.f, in1 ? w2[qh + xw1] : 0.f);
+                        if (n == 0) {
+                            ho0 = o1;
+                            ho1 = o2;
+                        } else {
+                            ho2 = o1;
+                            ho3 = o2;
                         }
+                        ++n;
                     }
                 }
             }
@@ -660,31 +675,11 @@ __global__ void __launch_bounds__(kThreads, 2)
                     const int e0 = a == 0 ? i0 : a == 1 ? kCfY + j : kCfZ + qq, e1 = a == 0 ? i0 + 1 : e0;
                     const f2 bb = pk(in0 ? s_cf[cur][0][e0] : 0.f, in1 ? s_cf[cur][0][e1] : 0.f);
                     const f2 cc = pk(in0 ? s_cf[cur][1][e0] : 0.f, in1 ? s_cf[cur][1][e1] : 0.f);
-                    // differences of E along a feeding the pair (c1, c2) of axis a
                     f2 d0, d1;
-                    if (a == 0) {
-                        const f2 ez = ld2(&s0.e[2][j][i0]), ey = ld2(&s0.e[1][j][i0]);
-                        d0 = sub2(pk(hi(ez), s0.e[2][j][i0 + 2]), ez);
-                        d1 = sub2(pk(hi(ey), s0.e[1][j][i0 + 2]), ey);
-                    } else if (a == 1) {
-                        d0 = sub2(ld2(&s0.e[2][j + 1][i0]), ld2(&s0.e[2][j][i0]));
-                        d1 = sub2(ld2(&s0.e[0][j + 1][i0]), ld2(&s0.e[0][j][i0]));
-                    } else {
-                        d0 = sub2(ld2(&s1.e[1][j][i0]), ld2(&s0.e[1][j][i0]));
-                        d1 = sub2(ld2(&s1.e[0][j][i0]), ld2(&s0.e[0][j][i0]));
-                    }
+                    e_diffs2(s0, s1, j, i0, a, d0, d1);
                     const f2 n0 = fma2(bb, ld2(P.psiB[pair_c1(a)][a] + q), mul2(cc, d0));
                     const f2 n1 = fma2(bb, ld2(P.psiB[pair_c2(a)][a] + q), mul2(cc, d1));
-                    if (a == 0) {
-                        nb.y = add2(nb.y, n0);
-                        nb.z = sub2(nb.z, n1);
-                    } else if (a == 1) {
-                        nb.x = sub2(nb.x, n0);
-                        nb.z = add2(nb.z, n1);
-                    } else {
-                        nb.x = add2(nb.x, n0);
-                        nb.y = sub2(nb.y, n1);
-                    }
+                    b_add_psi(a, n0, n1, nb);
                     if (own) {
                         const unsigned inm = (in0 ? 1u : 0u) | (in1 ? 2u : 0u);
                         st2m(O.psiB[pair_c1(a)][a] + q, n0, inm & mbits(mk, pair_c1(a)));
@@ -713,26 +708,30 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (hal) {
                 f2 hp0, hp1;
                 P3 h = b_pair(P, s0, s1, hj, hi0, sax, hbB, hcB, hp0, hp1);
-                if (kRare && sec) {
-                    V3 b[2] = {{lo(h.x), lo(h.y), lo(h.z)}, {hi(h.x), hi(h.y), hi(h.z)}};
+                if (kRare && sec) {   // further slab axes of the halo pair (their new memories: formed by the owner)
+                    int n = 0;
 #pragma unroll
-                    for (int p = 0; p < 2; ++p) {
-                        const int xw = wrap_or_out(P, 0, hgx0 + p), yw = wrap_or_out(P, 1, hgy);
-                        if (xw < 0 || yw < 0) continue;
-#pragma unroll 1
-                        for (int a = 0; a < 3; ++a) {
-                            if (!((sec >> a) & 1u)) continue;
-                            const int pos = a == 0 ? xw : a == 1 ? yw : k;
-                            float e0, e1;   // new halo memory: formed by the owner
-                            const int e = a == 0 ? hi0 + p : a == 1 ? kCfY + hj : kCfZ + qq;
-                            if (slab_pos(P, a, pos))
-                                b_psi_extra(P, s0, s1, hj, hi0 + p, a, s_cf[cur][0][e], s_cf[cur][1][e],
-                                            kq + yw * P.pitch + xw, b[p], e0, e1);
+                    for (int a = 0; a < 3; ++a) {
+                        if (!((sec >> a) & 1u)) continue;
+                        const unsigned m2 = (hin >> (2 * a)) & 3u;
+                        const f2 o1 = n == 0 ? ho0 : ho2, o2 = n == 0 ? ho1 : ho3;
+                        ++n;
+                        if (!m2) continue;
+                        f2 bb, cc;
+                        if (a == 0) {
+                            bb = ld2(&s_cf[cur][0][hi0]);
+                            cc = ld2(&s_cf[cur][1][hi0]);
+                        } else {
+                            const int e = a == 1 ? kCfY + hj : kCfZ + qq;
+                            bb = pk(s_cf[cur][0][e], s_cf[cur][0][e]);
+                            cc = pk(s_cf[cur][1][e], s_cf[cur][1][e]);
                         }
+                        bb = sel2(bb, 0, m2);
+                        cc = sel2(cc, 0, m2);
+                        f2 d0, d1;
+                        e_diffs2(s0, s1, hj, hi0, a, d0, d1);
+                        b_add_psi(a, fma2(bb, o1, mul2(cc, d0)), fma2(bb, o2, mul2(cc, d1)), h);
                     }
-                    h.x = pk(b[0].x, b[1].x);
-                    h.y = pk(b[0].y, b[1].y);
-                    h.z = pk(b[0].z, b[1].z);
                 }
                 if (masked) {
                     h.x = sel2(h.x, ld2(&s0.b[0][hj][hi0]), mbits(hmk, 0));
