@@ -166,8 +166,10 @@ tf_status tf_step(tf_handle h, int64_t nsteps);
  * nsteps exactly like tf_step and records a CUDA event pair on the handle's
  * stream around every kernel it launches.  On return (the stream is
  * synchronised) kernel_ms[k] is the mean duration in ms of one launch of
- * kernel kind k and launches[k] the number of launches, for k = 0 probe DFT,
- * 1 fused step (arrays of nkinds <= 2 entries). */
+ * kernel kind k and launches[k] the number of launches, for k = 0 a separate
+ * probe DFT kernel (no longer launched: the fused step adds E^n at the probes
+ * to their DFTs while its ring fills, so launches[0] stays 0) and k = 1 the
+ * fused step (arrays of nkinds <= 2 entries). */
 tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds);
 
 /* Advance n independent grids by nsteps steps each (the batched workload:

@@ -490,17 +490,16 @@ tf_status tf_add_probe(tf_handle h, int comp, const int p[3], const double* freq
 
 namespace {
 
-// per-step launch sequence (probe DFT of E^n, fused step, buffer swap); with
-// `ev` non-null an event is recorded before, between and after the launches
+// per-step launch sequence (fused step with the probe DFT of E^n, buffer
+// swap); with `ev` non-null events are recorded before and after the launch
 cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
     cudaStream_t st = h->stream;
     cudaError_t e = cudaSuccess;
     if (ev) cudaEventRecord(ev[0], st);
-    if (h->R.n) e = launch_probe(h->P, h->R, h->level, st);
     if (ev) cudaEventRecord(ev[1], st);
     const double t1 = (double)(h->level + 1) * h->dt;
     for (int q = 0; q < h->nsrc; ++q) S.amp[q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
-    if (e == cudaSuccess) e = launch_step(h->tmap[0], h->P, h->O, S, h->step_blocks, st);
+    if (e == cudaSuccess) e = launch_step(h->tmap[0], h->P, h->O, S, h->R, h->level, h->step_blocks, st);
     if (ev) cudaEventRecord(ev[2], st);
     // the new state is in O's buffers: swap
     for (int c = 0; c < 3; ++c) {
@@ -619,7 +618,7 @@ tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t*
             if (cudaEventCreate(&ev[created][m]) != cudaSuccess) ok = false;
         if (!ok) { rc = TF_ECUDA; ++created; break; }
     }
-    const int has[2] = {h->R.n > 0, 1};
+    const int has[2] = {0, 1};   // the probes are sampled inside the step: no launch of their own
     Sources S;
     fill_sources(h, S);
     if (refresh_order(h, S) != cudaSuccess) rc = TF_ECUDA;

@@ -135,6 +135,21 @@ struct Probes {
     double dt;
 };
 
+// running DFT of probe pr at level n (Secs. 4.2, 5): X_f += s^n e^{-2 pi i f_k n dt} dt in FP64,
+// for the frequency f handled by this thread, and the series sample (f = 0)
+__device__ __forceinline__ void probe_update(const float* const E[3], const Probes& R, int pr, int f, long long n) {
+    const double s = (double)E[R.comp[pr]][R.q[pr]];
+    if (f == 0 && n < R.cap) R.series[(long long)pr * R.cap + n] = s;
+    if (f < R.nfreq[pr] && n >= R.n0[pr]) {
+        double ph = R.fdt[pr * TF_MAX_FREQS + f] * (double)n;
+        ph -= floor(ph);
+        double sn, cs;
+        sincospi(2.0 * ph, &sn, &cs);
+        R.re[pr * TF_MAX_FREQS + f] += s * cs * R.dt;
+        R.im[pr * TF_MAX_FREQS + f] -= s * sn * R.dt;
+    }
+}
+
 __host__ __device__ __forceinline__ long long lin(const Params& P, int i, int j, int k) {
     return (long long)k * P.plane + (long long)j * P.pitch + i;
 }
@@ -247,14 +262,15 @@ cudaError_t launch_prime(const Params& P, cudaStream_t st);
 cudaError_t launch_mask_js(const Params& P, cudaStream_t st);
 cudaError_t launch_read_field(const Params& P, int comp, int primed, float* dense, double scale,
                               cudaStream_t st);
-cudaError_t launch_probe(const Params& P, const Probes& R, long long n, cudaStream_t st);
 // 4-D TMA view (x, y, z, array index) of `narrays` equally spaced arrays with
 // a box of bx x by x 1 x bf; writes a 128-byte CUtensorMap to out128
 cudaError_t make_tensor_map(void* base, const int N[3], int pitch, size_t array_bytes, int narrays, int bx,
                             int by, int bf, void* out128);
 // tmaps: three consecutive 128-byte maps -- E box, B box, psi_B box
-cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, const Sources& S, int blocks,
-                        cudaStream_t st);
+// one fused step from level n; the step also adds E^n at the probe points to
+// their running DFTs and series
+cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, const Sources& S, const Probes& R,
+                        long long n, int blocks, cudaStream_t st);
 cudaError_t launch_edge_coeffs(const Params& P, cudaStream_t st);
 size_t step_smem_bytes();
 cudaError_t launch_tile_materials(const Params& P, float4* tilemat, int ntx, int nty, cudaStream_t st);

@@ -1,8 +1,7 @@
 // tf_kernels.cu -- CUDA kernels of the two-fluid Yee library for sm_103a.
 //
 // The per-step kernels besides the fused step of tf_step.cu:
-//   k_probe     running FP64 DFT of E^n at the probe points (Secs. 4.2, 5)
-// plus set-up and read-back kernels (material scaling, level-0 priming
+// set-up and read-back kernels (material scaling, level-0 priming
 // B^{-1/2} = B^0 + dt/2 curl E^0 and Js^{-1/2} = Js^0 - dt/2 kappa E^0, and
 // integer-level read-back B^n = B^{n-1/2} - dt/2 curl E^n,
 // Js^n = Js^{n-1/2} + dt/2 kappa E^n).
@@ -185,21 +184,6 @@ __global__ void k_read_field(Params P, int comp, int primed, float* dense, doubl
 }
 
 // ------------------------------------------------------------ time step
-__global__ void k_probe(Params P, Probes R, long long n) {
-    const int pr = blockIdx.x, f = threadIdx.x;
-    if (pr >= R.n) return;
-    const double s = (double)P.E[R.comp[pr]][R.q[pr]];
-    if (f == 0 && n < R.cap) R.series[(long long)pr * R.cap + n] = s;
-    if (f < R.nfreq[pr] && n >= R.n0[pr]) {
-        double ph = R.fdt[pr * TF_MAX_FREQS + f] * (double)n;
-        ph -= floor(ph);
-        double sn, cs;
-        sincospi(2.0 * ph, &sn, &cs);
-        R.re[pr * TF_MAX_FREQS + f] += s * cs * R.dt;
-        R.im[pr * TF_MAX_FREQS + f] -= s * sn * R.dt;
-    }
-}
-
 // ------------------------------------------------------------ launchers
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
@@ -241,9 +225,5 @@ cudaError_t launch_read_field(const Params& P, int comp, int primed, float* dens
     return cudaGetLastError();
 }
 
-cudaError_t launch_probe(const Params& P, const Probes& R, long long n, cudaStream_t st) {
-    k_probe<<<R.n, TF_MAX_FREQS, 0, st>>>(P, R, n);
-    return cudaGetLastError();
-}
 
 }  // namespace tf

@@ -345,7 +345,7 @@ __device__ __forceinline__ bool item_is_rare(const Params& P, const Sources& S, 
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 2)
-    k_step(const __grid_constant__ TMaps tm, Params P, StepOut O, Sources S) {
+    k_step(const __grid_constant__ TMaps tm, Params P, StepOut O, Sources S, Probes R, long long level) {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // TMA destinations must be 128-byte aligned: round the base up (128 spare bytes are allocated)
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
@@ -480,6 +480,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     if (tid == kProd) pump();
     __syncthreads();
+    // while the ring fills: E^n at the probe points into their DFTs, a probe per CTA
+    if (tid < TF_MAX_FREQS)
+        for (int pr = blockIdx.x; pr < R.n; pr += gridDim.x) probe_update(P.E, R, pr, tid, level);
 
     int cur = 0;
     bool aborted = false;
@@ -1049,12 +1052,12 @@ cudaError_t make_tensor_map(void* base, const int N[3], int pitch, size_t array_
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, const Sources& S, int blocks,
-                        cudaStream_t st) {
+cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, const Sources& S, const Probes& R,
+                        long long n, int blocks, cudaStream_t st) {
     static cudaError_t attr = step_smem_attribute();
     if (attr != cudaSuccess) return attr;
     const TMaps* tm = (const TMaps*)tmaps;
-    k_step<<<blocks, dim3(kTX, kThreadsY), step_smem_bytes(), st>>>(*tm, P, O, S);
+    k_step<<<blocks, dim3(kTX, kThreadsY), step_smem_bytes(), st>>>(*tm, P, O, S, R, n);
     return cudaGetLastError();
 }
 
@@ -1071,8 +1074,8 @@ __global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Source
     const int a = min((int)threadIdx.x * per, n), b = min(a + per, n);
     const bool mur = P.bc[2] == TF_BC_MUR;
     auto chunk = [&](int d, int& tile, int& kz0, int& len) {
-        tile = d / O.nch;
-        kz0 = (d % O.nch) * kChunk;
+        tile = d % (O.ntx * O.nty);
+        kz0 = (d / (O.ntx * O.nty)) * kChunk;
         len = min(kChunk, O.kend - kz0);
     };
     int ns = 0, nf = 0;
