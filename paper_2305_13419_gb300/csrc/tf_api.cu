@@ -523,7 +523,10 @@ cudaError_t refresh_order(tf_ctx* h, const Sources& S) {
     // fewer than 8 (tile, chunk) items per CTA: cut the slow ones into pieces
     const long long items = (long long)h->L.ntx * h->L.nty * h->L.nch;
     const int split = items < 8LL * h->step_blocks;
-    cudaError_t e = launch_item_order(h->P, h->O, S, split, (int*)h->O.order, dcount, h->stream);
+    // the last plain items of the order, one per CTA, also go out in pieces:
+    // the CTAs then run out of work at nearly the same time
+    const int tail = h->step_blocks;
+    cudaError_t e = launch_item_order(h->P, h->O, S, split, tail, (int*)h->O.order, dcount, h->stream);
     int n = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&n, dcount, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -298,7 +298,7 @@ cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0
                                  cudaStream_t stream);
 
 // order in which k_step hands out its work items (items needing the full plane loop first)
-cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int* order,
+cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int tail, int* order,
                               int* count, cudaStream_t st);
 int step_blocks_per_sm();
 cudaError_t launch_field_stats(const float* f, int n0, int n1, int n2, int pitch, long long plane, double scale,

@@ -1066,23 +1066,34 @@ cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, co
 // few items per CTA (`split`) each cut into kSub-plane pieces, so that their
 // long bodies run side by side -- then the others, whole.  One CTA; writes
 // the descriptors and their count.
-__global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Sources S, int split, int* order,
+__global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Sources S, int split, int tail, int* order,
                                                     int* count) {
-    __shared__ int s_slow[1024], s_fast[1024];
-    const int n = O.ntx * O.nty * O.nch;
+    __shared__ int s_slow[1024], s_fast[1024], s_tail[1024];
+    const int n = O.ntx * O.nty * O.nch, ntiles = O.ntx * O.nty;
     const int per = (n + 1023) / 1024;
     const int a = min((int)threadIdx.x * per, n), b = min(a + per, n);
     const bool mur = P.bc[2] == TF_BC_MUR;
     auto chunk = [&](int d, int& tile, int& kz0, int& len) {
-        tile = d % (O.ntx * O.nty);
-        kz0 = (d / (O.ntx * O.nty)) * kChunk;
+        tile = d % ntiles;
+        kz0 = (d / ntiles) * kChunk;
         len = min(kChunk, O.kend - kz0);
+    };
+    auto rare_of = [&](int tile, int kz0, int len) {
+        return item_is_rare(P, S, mur, tile_of(P, O, make_item(tile, kz0, len)));
+    };
+    auto scan = [&](int* v) {   // inclusive prefix sum over the block
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int x = (int)threadIdx.x >= off ? v[threadIdx.x - off] : 0;
+            __syncthreads();
+            v[threadIdx.x] += x;
+            __syncthreads();
+        }
     };
     int ns = 0, nf = 0;
     for (int d = a; d < b; ++d) {
         int tile, kz0, len;
         chunk(d, tile, kz0, len);
-        if (item_is_rare(P, S, mur, tile_of(P, O, make_item(tile, kz0, len))))
+        if (rare_of(tile, kz0, len))
             ns += split ? (len + kSub - 1) / kSub : 1;
         else
             nf += 1;
@@ -1090,33 +1101,48 @@ __global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Source
     s_slow[threadIdx.x] = ns;
     s_fast[threadIdx.x] = nf;
     __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const int vs = (int)threadIdx.x >= off ? s_slow[threadIdx.x - off] : 0;
-        const int vf = (int)threadIdx.x >= off ? s_fast[threadIdx.x - off] : 0;
-        __syncthreads();
-        s_slow[threadIdx.x] += vs;
-        s_fast[threadIdx.x] += vf;
-        __syncthreads();
+    scan(s_slow);
+    scan(s_fast);
+    const int total_slow = s_slow[1023], total_fast = s_fast[1023];
+    const int cut = total_fast - min(tail, total_fast);   // fast items from this rank on are cut into pieces
+    int nt = 0;
+    {
+        int rank = s_fast[threadIdx.x] - nf;
+        for (int d = a; d < b; ++d) {
+            int tile, kz0, len;
+            chunk(d, tile, kz0, len);
+            if (rare_of(tile, kz0, len)) continue;
+            if (rank >= cut) nt += (len + kSub - 1) / kSub;
+            ++rank;
+        }
     }
-    const int total_slow = s_slow[1023];
-    int r = s_slow[threadIdx.x] - ns;                // slow pieces before this thread's range
-    int c = total_slow + s_fast[threadIdx.x] - nf;   // position of its first whole item
+    s_tail[threadIdx.x] = nt;
+    __syncthreads();
+    scan(s_tail);
+    int r = s_slow[threadIdx.x] - ns;                     // slow pieces before this thread's range
+    int rank = s_fast[threadIdx.x] - nf;                  // fast items before it
+    int c = total_slow + cut + s_tail[threadIdx.x] - nt;  // position of its first tail piece
     for (int d = a; d < b; ++d) {
         int tile, kz0, len;
         chunk(d, tile, kz0, len);
-        if (item_is_rare(P, S, mur, tile_of(P, O, make_item(tile, kz0, len)))) {
+        if (rare_of(tile, kz0, len)) {
             const int piece = split ? kSub : len;
             for (int k = kz0; k < kz0 + len; k += piece) order[r++] = make_item(tile, k, min(piece, kz0 + len - k));
         } else {
-            order[c++] = make_item(tile, kz0, len);
+            if (rank < cut) {
+                order[total_slow + rank] = make_item(tile, kz0, len);
+            } else {
+                for (int k = kz0; k < kz0 + len; k += kSub) order[c++] = make_item(tile, k, min(kSub, kz0 + len - k));
+            }
+            ++rank;
         }
     }
-    if (threadIdx.x == 1023) *count = total_slow + s_fast[1023];
+    if (threadIdx.x == 1023) *count = total_slow + cut + s_tail[1023];
 }
 
-cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int* order,
+cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int tail, int* order,
                               int* count, cudaStream_t st) {
-    k_item_order<<<1, 1024, 0, st>>>(P, O, S, split, order, count);
+    k_item_order<<<1, 1024, 0, st>>>(P, O, S, split, tail, order, count);
     return cudaGetLastError();
 }
 
