@@ -1064,8 +1064,10 @@ cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, co
 // work items of a launch, in the order they are handed out: the (tile, z
 // chunk) items that need the full plane loop come first -- on a grid with
 // few items per CTA (`split`) each cut into kSub-plane pieces, so that their
-// long bodies run side by side -- then the others, whole.  One CTA; writes
-// the descriptors and their count.
+// long bodies run side by side -- then the others, z chunk by z chunk (the
+// CTAs at work at one time then share halos in L2), the last `tail` of them
+// cut into kSub-plane pieces so that the CTAs run out of work together.
+// One CTA; writes the descriptors and their count.
 __global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Sources S, int split, int tail, int* order,
                                                     int* count) {
     __shared__ int s_slow[1024], s_fast[1024], s_tail[1024];
