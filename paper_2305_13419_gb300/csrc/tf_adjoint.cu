@@ -22,10 +22,13 @@
 // and the gradient of the objective collects, per edge,
 //   dJ/d eps_e += Eh' cb (E^n - E'_no-source)     (Alg. 1 step 3, theta scheme)
 //   dJ/d kt_e  += Jh E^n                           (steps 4 + 2)
-// The face pass writes Bh'tot and psi_Bh'tot in place (the bB factor of the
-// next step is applied when psi_Bh is next read); the edge pass reads its own
-// edge and the faces around it, so both update in place.  One thread per
-// storage point handles its three components.
+// Each pass forms, once per point, the weights the other pass differences:
+// the face pass stores the face weights u_c,a = -curl_sign r_a Bh'tot +
+// cB psi_Bh'tot (zero on faces the step leaves alone), the edge pass the edge
+// weights w_e,a = sE r_a e + cE psi_Eh'tot of the next step (zero on edges the
+// step leaves alone); a pass then reads its neighbours' weights as plain
+// loads.  Both passes update in place; one thread per storage point handles
+// its three components, a block covers 32 x 8 points of one plane.
 #include <math.h>
 
 #include "tf_internal.cuh"
@@ -34,77 +37,65 @@ namespace tf {
 
 namespace {
 
-constexpr int kAdjThreads = 256;
+constexpr int kAX = 32, kAY = 8;
 
-__device__ __forceinline__ void point_of(const Params& P, long long t, int p[3]) {
-    const long long xy = (long long)P.pitch * P.N[1];
-    p[2] = (int)(t / xy);
-    const long long r = t - (long long)p[2] * xy;
-    p[1] = (int)(r / P.pitch);
-    p[0] = (int)(r - (long long)p[1] * P.pitch);
+// storage point of this thread (3-D launch: x, y blocks, one plane per blockIdx.z)
+__device__ __forceinline__ bool point_of(const Params& P, int p[3]) {
+    p[0] = blockIdx.x * kAX + threadIdx.x;
+    p[1] = blockIdx.y * kAY + threadIdx.y;
+    p[2] = blockIdx.z;
+    return p[0] < P.N[0] && p[1] < P.N[1];
 }
 
-// weight on dH_a(H_h)(x) of edge e at x (h = 3 - e - a), zero for edges the step leaves alone
-__device__ __forceinline__ float edge_weight(const Params& P, const AdjState& A, int e, int a, const int x[3]) {
-    const long long q = lin(P, x[0], x[1], x[2]);
-    const float cb = __ldg(P.cb[e] + q);
-    if (cb == 0.f) return 0.f;
-    const float s = curl_sign(e, a);
-    const float ev = cb * A.E[e][q];
-    float w = s * P.r[a] * ev;
-    if (A.psiE[e][a] && in_slab(P, a, x[a])) w += __ldg(P.pcE[a] + x[a]) * (A.psiE[e][a][q] + s * ev);
-    return w;
-}
-
-// weight on dE_a(E_e)(y) of face c at y (e = 3 - c - a), zero for faces the step leaves alone
-__device__ __forceinline__ float face_weight(const Params& P, const AdjState& A, int c, int a, const int y[3]) {
-    if (!upd_B(P, c, y)) return 0.f;
-    const long long q = lin(P, y[0], y[1], y[2]);
-    float u = -curl_sign(c, a) * P.r[a] * A.B[c][q];
-    if (A.psiB[c][a] && in_slab(P, a, y[a])) u += __ldg(P.pcB[a] + y[a]) * A.psiB[c][a][q];
-    return u;
+__device__ __forceinline__ int lin32(const Params& P, int i, int j, int k) {
+    return k * (int)P.plane + j * P.pitch + i;
 }
 
 }  // namespace
 
-// face pass: Bh'tot = Bh' + (1/mu) sum_a [w(y) - w(y + a)], psi_Bh'tot
-__global__ void __launch_bounds__(kAdjThreads) k_adj_faces(Params P, AdjState A) {
-    const long long t = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
-    if (t >= (long long)P.plane * P.N[2]) return;
+// face pass: Bh'tot = Bh' + (1/mu) sum_a [w(p) - w(p + a)], psi_Bh'tot, and the face weights
+__global__ void __launch_bounds__(kAX * kAY) k_adj_faces(Params P, AdjState A) {
     int p[3];
-    point_of(P, t, p);
-    if (p[0] >= P.N[0]) return;
-    const long long q = lin(P, p[0], p[1], p[2]);
+    if (!point_of(P, p)) return;
+    const int q = lin32(P, p[0], p[1], p[2]);
+    // the next point along each axis (clamped at a wall, where the difference vanishes)
+    const int qn[3] = {lin32(P, nxt(P, 0, p[0]), p[1], p[2]), lin32(P, p[0], nxt(P, 1, p[1]), p[2]),
+                       lin32(P, p[0], p[1], nxt(P, 2, p[2]))};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        if (!upd_B(P, c, p)) continue;
-        float hsum = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (a == c) continue;
-            const int e = 3 - c - a;
-            int x[3] = {p[0], p[1], p[2]};
-            x[a] = nxt(P, a, p[a]);
-            hsum += edge_weight(P, A, e, a, p) - edge_weight(P, A, e, a, x);
-        }
+        if (!upd_B(P, c, p)) continue;   // its weights stay zero
+        const int a1 = (c + 1) % 3, a2 = (c + 2) % 3;
+        const int e1 = 3 - c - a1, e2 = 3 - c - a2;
+        const float hsum = (A.W[e1][a1][q] - A.W[e1][a1][qn[a1]]) + (A.W[e2][a2][q] - A.W[e2][a2][qn[a2]]);
         const float bt = A.B[c][q] + hsum * inv_mu_face(P, c, p);
         A.B[c][q] = bt;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (a == c || !A.psiB[c][a] || !in_slab(P, a, p[a])) continue;
-            A.psiB[c][a][q] = __ldg(P.pbB[a] + p[a]) * A.psiB[c][a][q] - curl_sign(c, a) * bt;
+        for (int t = 0; t < 2; ++t) {
+            const int a = t ? a2 : a1;
+            const float sg = curl_sign(c, a);
+            float u = -sg * P.r[a] * bt;
+            if (A.psiB[c][a] && in_slab(P, a, p[a])) {
+                const float ps = __ldg(P.pbB[a] + p[a]) * A.psiB[c][a][q] - sg * bt;
+                A.psiB[c][a][q] = ps;
+                u += __ldg(P.pcB[a] + p[a]) * ps;
+            }
+            A.U[c][a][q] = u;
         }
     }
 }
 
-// edge pass: Jh, psi_Eh, Eh; per-edge gradients; the objective's derivative at the probe
-__global__ void __launch_bounds__(kAdjThreads) k_adj_edges(Params P, AdjState A, Sources S, AdjStep st) {
-    const long long t = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
-    if (t >= (long long)P.plane * P.N[2]) return;
+// edge pass: Jh, psi_Eh, Eh; per-edge gradients; the objective's derivative
+// at the probe; the edge weights of the next step
+__global__ void __launch_bounds__(kAX * kAY) k_adj_edges(Params P, AdjState A, Sources S, AdjStep st) {
     int p[3];
-    point_of(P, t, p);
-    if (p[0] >= P.N[0]) return;
-    const long long q = lin(P, p[0], p[1], p[2]);
+    if (!point_of(P, p)) return;
+    const int q = lin32(P, p[0], p[1], p[2]);
+    // the previous point along each axis (none below a wall)
+    const int qp[3] = {lin32(P, prv(P, 0, p[0]), p[1], p[2]), lin32(P, p[0], prv(P, 1, p[1]), p[2]),
+                       lin32(P, p[0], p[1], prv(P, 2, p[2]))};
+    const bool hp[3] = {P.per[0] || p[0] > 0, P.per[1] || p[1] > 0, P.per[2] || p[2] > 0};
+    const bool in_src = S.n > 0 && p[0] >= S.bb_lo[0] && p[0] <= S.bb_hi[0] && p[1] >= S.bb_lo[1] &&
+                        p[1] <= S.bb_hi[1] && p[2] >= S.bb_lo[2] && p[2] <= S.bb_hi[2];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         const float ep = A.E[e][q];
@@ -114,12 +105,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_edges(Params P, AdjState A,
         for (int a = 0; a < 3; ++a) {
             if (a == e) continue;
             const int c = 3 - e - a;
-            if (P.per[a] || p[a] > 0) {
-                int y[3] = {p[0], p[1], p[2]};
-                y[a] = prv(P, a, p[a]);
-                d += face_weight(P, A, c, a, y);
-            }
-            d -= face_weight(P, A, c, a, p);
+            if (hp[a]) d += A.U[c][a][qp[a]];
+            d -= A.U[c][a][q];
         }
         const float cb = __ldg(P.cb[e] + q);
         float enew = ep + d;
@@ -136,24 +123,36 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_edges(Params P, AdjState A,
             // gradients: E^n, and E^{n+1} without this step's soft sources
             const float en = st.En[e][q];
             float e1 = st.En1[e][q];
-            for (int s = 0; s < S.n; ++s)
-                if (S.comp[s] == e && p[0] >= S.lo[s][0] && p[0] < S.hi[s][0] && p[1] >= S.lo[s][1] &&
-                    p[1] < S.hi[s][1] && p[2] >= S.lo[s][2] && p[2] < S.hi[s][2])
-                    e1 -= S.amp[s];
+            if (in_src)
+                for (int s = 0; s < S.n; ++s)
+                    if (S.comp[s] == e && p[0] >= S.lo[s][0] && p[0] < S.hi[s][0] && p[1] >= S.lo[s][1] &&
+                        p[1] < S.hi[s][1] && p[2] >= S.lo[s][2] && p[2] < S.hi[s][2])
+                        e1 -= S.amp[s];
             A.gE[e][q] += (double)ep * (double)cb * (double)(en - e1);
             if (cj > 0.f) A.gK[e][q] += (double)jh * (double)en;
         }
         if (e == st.probe_comp && q == st.probe_q) enew += st.probe_src;
         A.E[e][q] = enew;
+        if (cb != 0.f) {   // edge weights of the next face pass (they stay zero where cb = 0)
+            const float evn = cb * enew;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a == e) continue;
+                const float sg = curl_sign(e, a);
+                float w = sg * P.r[a] * evn;
+                if (A.psiE[e][a] && in_slab(P, a, p[a])) w += __ldg(P.pcE[a] + p[a]) * (A.psiE[e][a][q] + sg * evn);
+                A.W[e][a][q] = w;
+            }
+        }
     }
 }
 
 // per cell: dJ/d eps_r and dJ/d lambda_L from the per-edge sums, with the
 // weights of the edge rule (eps: mean of 4 cells; kt: mean over the 4 cells
 // or over the superconducting ones)
-__global__ void __launch_bounds__(kAdjThreads) k_adj_cells(Params P, AdjState A, float dt_c0, float* g_eps,
+__global__ void __launch_bounds__(256) k_adj_cells(Params P, AdjState A, float dt_c0, float* g_eps,
                                                           float* g_lam) {
-    const long long t = (long long)blockIdx.x * kAdjThreads + threadIdx.x;
+    const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
     const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
     if (t >= nc) return;
     const int cell[3] = {(int)(t % P.n[0]), (int)((t / P.n[0]) % P.n[1]), (int)(t / ((long long)P.n[0] * P.n[1]))};
@@ -206,22 +205,18 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_cells(Params P, AdjState A,
     g_lam[t] = gl;
 }
 
-static unsigned adj_blocks(const Params& P) {
-    return (unsigned)(((long long)P.plane * P.N[2] + kAdjThreads - 1) / kAdjThreads);
-}
-
 cudaError_t launch_adjoint_step(const Params& P, const AdjState& A, const Sources& S, const AdjStep& st,
                                 cudaStream_t stream) {
-    k_adj_faces<<<adj_blocks(P), kAdjThreads, 0, stream>>>(P, A);
-    k_adj_edges<<<adj_blocks(P), kAdjThreads, 0, stream>>>(P, A, S, st);
+    const dim3 grid((P.N[0] + kAX - 1) / kAX, (P.N[1] + kAY - 1) / kAY, P.N[2]), block(kAX, kAY);
+    k_adj_faces<<<grid, block, 0, stream>>>(P, A);
+    k_adj_edges<<<grid, block, 0, stream>>>(P, A, S, st);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0, float* g_eps, float* g_lam,
                                  cudaStream_t stream) {
     const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
-    k_adj_cells<<<(unsigned)((nc + kAdjThreads - 1) / kAdjThreads), kAdjThreads, 0, stream>>>(P, A, dt_c0, g_eps,
-                                                                                              g_lam);
+    k_adj_cells<<<(unsigned)((nc + 255) / 256), 256, 0, stream>>>(P, A, dt_c0, g_eps, g_lam);
     return cudaGetLastError();
 }
 

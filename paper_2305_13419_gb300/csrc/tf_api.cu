@@ -847,7 +847,7 @@ AdjLayout adj_layout(const tf_ctx* h, int64_t nsteps, int segment) {
     size_t o = 0;
     A.off_ck = o;    o += A.nck * A.ck;
     A.off_hist = o;  o += (size_t)(segment + 1) * 3 * fb;
-    A.off_state = o; o += (size_t)(9 + 4 * h->L.ncpml_axes) * fb;
+    A.off_state = o; o += (size_t)(9 + 4 * h->L.ncpml_axes + 12) * fb;   // E, B, J, psi, edge and face weights
     A.off_grad = o;  o += 6 * align_up(sizeof(double) * (size_t)h->L.total);
     A.bytes = o;
     return A;
@@ -909,6 +909,13 @@ tf_status tf_adjoint_run(tf_handle h, int64_t nsteps, int probe, int freq_index,
                 S.psiE[c][a] = fa();
             }
         }
+        for (int c = 0; c < 3; ++c)
+            for (int a = 0; a < 3; ++a) {
+                S.W[c][a] = S.U[c][a] = nullptr;
+                if (a == c) continue;
+                S.W[c][a] = fa();
+                S.U[c][a] = fa();
+            }
         for (int c = 0; c < 3; ++c) {
             S.gE[c] = (double*)(sc + A.off_grad + (size_t)c * gb);
             S.gK[c] = (double*)(sc + A.off_grad + (size_t)(3 + c) * gb);

@@ -284,6 +284,8 @@ struct AdjState {
     float* psiE[3][3];
     double* gE[3];       // dJ / d eps_r,e
     double* gK[3];       // dJ / d kt_e
+    float* W[3][3];      // edge weights [e][a] (a != e) the face pass differences
+    float* U[3][3];      // face weights [c][a] (a != c) the edge pass differences
 };
 struct AdjStep {
     const float* En[3];    // E^n
