@@ -511,7 +511,10 @@ cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
     h->O.psib_cur = h->parity ? 2 : 0;
     h->O.ecur = h->parity ? 9 : 0;
     h->O.bcur = h->parity ? 12 : 3;
-    h->O.base += (unsigned long long)h->O.nitems + (unsigned long long)h->step_blocks;
+    // the counter moved once per item past the 2G handed out at the start,
+    // and once more (the fetch that came back empty) in every CTA that used it
+    const long long ni = h->O.nitems, g = h->step_blocks;
+    h->O.base += (unsigned long long)((ni > 2 * g ? ni - 2 * g : 0) + (ni - g < 0 ? 0 : ni - g > g ? g : ni - g));
     h->level++;
     return e;
 }

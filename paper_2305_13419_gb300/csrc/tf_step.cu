@@ -365,8 +365,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int PL = (int)P.plane;
     const bool mur = P.bc[2] == TF_BC_MUR;
 
+    // Items 0 .. 2G - 1 (G CTAs) are handed out without the counter: CTA b
+    // starts with items b and G + b.  The others come from the counter.
     auto fetch = [&]() -> int {   // producer: next work item or -1 (items that take the full loop come first)
-        const long long d = (long long)(atomicAdd(O.ctr, 1ull) - O.base);
+        const long long d = (long long)(atomicAdd(O.ctr, 1ull) - O.base) + 2LL * gridDim.x;
         return (d >= 0 && d < nitems) ? __ldg(O.order + d) : -1;
     };
     // the records of an item: loaded by threads < nq - 1 ...
@@ -466,8 +468,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (tid == kProd) {
         for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_item[0] = fetch();
-        s_item[1] = s_item[0] >= 0 ? fetch() : -1;
+        const int b = (int)blockIdx.x, g = (int)gridDim.x;
+        s_item[0] = b < nitems ? __ldg(O.order + b) : -1;
+        s_item[1] = (s_item[0] >= 0 && g + b < nitems) ? __ldg(O.order + g + b) : -1;
     }
     __syncthreads();
     {
