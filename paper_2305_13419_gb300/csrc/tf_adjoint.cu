@@ -205,6 +205,27 @@ __global__ void __launch_bounds__(256) k_adj_cells(Params P, AdjState A, float d
     g_lam[t] = gl;
 }
 
+// E^n of the three components into the adjoint's history (16-byte aligned
+// arrays of n4 float4 each), grid-stride
+__global__ void __launch_bounds__(256) k_copy3(float4* d0, float4* d1, float4* d2, const float4* s0, const float4* s1,
+                                               const float4* s2, long long n4) {
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n4; i += (long long)gridDim.x * 256) {
+        const float4 a = __ldg(s0 + i), b = __ldg(s1 + i), c = __ldg(s2 + i);
+        d0[i] = a;
+        d1[i] = b;
+        d2[i] = c;
+    }
+}
+
+cudaError_t launch_copy3(float* const dst[3], float* const src[3], long long n, cudaStream_t stream) {
+    if (n % 4 != 0) return cudaErrorInvalidValue;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess || sms < 1) sms = 1;
+    k_copy3<<<4 * sms, 256, 0, stream>>>((float4*)dst[0], (float4*)dst[1], (float4*)dst[2], (const float4*)src[0],
+                                          (const float4*)src[1], (const float4*)src[2], n / 4);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint_step(const Params& P, const AdjState& A, const Sources& S, const AdjStep& st,
                                 cudaStream_t stream) {
     const dim3 grid((P.N[0] + kAX - 1) / kAX, (P.N[1] + kAY - 1) / kAY, P.N[2]), block(kAX, kAY);

@@ -933,9 +933,8 @@ tf_status tf_adjoint_run(tf_handle h, int64_t nsteps, int probe, int freq_index,
         if ((rc = tf_checkpoint_load(h, sc + A.off_ck + s * A.ck, A.ck, 1)) != TF_OK) return rc;
         const int64_t len = (s + 1) * segment <= nsteps ? segment : nsteps - s * segment;
         for (int64_t m = 0; m <= len; ++m) {
-            for (int c = 0; c < 3; ++c)
-                TF_CUDA(cudaMemcpyAsync(hist(m, c), h->P.E[c], sizeof(float) * (size_t)h->L.total,
-                                        cudaMemcpyDeviceToDevice, h->stream));
+            float* const dst[3] = {hist(m, 0), hist(m, 1), hist(m, 2)};
+            TF_CUDA(launch_copy3(dst, h->P.E, h->L.total, h->stream));
             if (m < len && (rc = tf_step(h, 1)) != TF_OK) return rc;
         }
         // adjoint steps back through the segment

@@ -296,6 +296,8 @@ struct AdjStep {
 };
 cudaError_t launch_adjoint_step(const Params& P, const AdjState& A, const Sources& S, const AdjStep& st,
                                 cudaStream_t stream);
+// copy three float arrays of n elements (n a multiple of 4, 16-byte aligned)
+cudaError_t launch_copy3(float* const dst[3], float* const src[3], long long n, cudaStream_t stream);
 cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0, float* g_eps, float* g_lam,
                                  cudaStream_t stream);
 
