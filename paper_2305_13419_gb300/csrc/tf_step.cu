@@ -367,8 +367,12 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     // Items 0 .. 2G - 1 (G CTAs) are handed out without the counter: CTA b
     // starts with items b and G + b.  The others come from the counter.
-    auto fetch = [&]() -> int {   // producer: next work item or -1 (items that take the full loop come first)
-        const long long d = (long long)(atomicAdd(O.ctr, 1ull) - O.base) + 2LL * gridDim.x;
+    // producer: a ticket from the counter, and later the work item it names
+    // (or -1); the two halves are a plane apart, so that the counter's round
+    // trip does not hold up the producer's warp
+    auto ticket = [&]() -> unsigned long long { return atomicAdd(O.ctr, 1ull); };
+    auto item_of = [&](unsigned long long tk) -> int {
+        const long long d = (long long)(tk - O.base) + 2LL * gridDim.x;
         return (d >= 0 && d < nitems) ? __ldg(O.order + d) : -1;
     };
     // the records of an item: loaded by threads < nq - 1 ...
@@ -492,6 +496,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     unsigned long long seq0 = 0;   // ring sequence number of plane 0 of the current item
     unsigned it = 0;               // planes done by this CTA (selects the shared B plane)
     int pend = -1;                 // producer: the item after the next one
+    unsigned long long ptk = 0;    // producer: its ticket
+    bool phas = false;             // producer: a ticket was drawn for it
     while (true) {
         const int item = s_item[cur];
         if (item < 0) break;
@@ -756,7 +762,11 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (tid == kProd) {
                 consumed = g0;
                 pump();
-                if (qq == 0) pend = s_item[cur ^ 1] >= 0 ? fetch() : -1;
+                if (qq == 0) {
+                    phas = s_item[cur ^ 1] >= 0;
+                    if (phas) ptk = ticket();
+                }
+                if (qq == 1 || nq == 2) pend = phas ? item_of(ptk) : -1;
             }
             if (qq == 0) rec_load(s_item[cur ^ 1], rnext, cfnext);
 
