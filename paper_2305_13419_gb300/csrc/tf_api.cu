@@ -131,6 +131,7 @@ struct tf_ctx {
     long long level;
     int primed;
     int order_dirty;   // the work-item order must be rebuilt before the next step
+    int fine;          // fewer items than CTA slots: every item goes out in pieces
     char* ws;
     float* scratch;
     unsigned* status;
@@ -342,8 +343,12 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
             return TF_ECUDA;
         }
         // one resident CTA per slot, but no more than half the items: a small
-        // grid then leaves SMs to grids stepping on other streams
-        long long nb = (long long)sms * per_sm, half = (items + 1) / 2;
+        // grid then leaves SMs to grids stepping on other streams.  A grid
+        // with fewer items than slots goes out in kSub-plane pieces.
+        const long long slots = (long long)sms * per_sm;
+        h->fine = items < slots;
+        const long long units = h->fine ? items * ((kChunk + kSub - 1) / kSub) : items;
+        long long nb = slots, half = (units + 1) / 2;
         if (half < nb) nb = half;
         h->step_blocks = (int)(nb > 0 ? nb : 1);
     }
@@ -528,7 +533,7 @@ cudaError_t refresh_order(tf_ctx* h, const Sources& S) {
     const int split = items < 8LL * h->step_blocks;
     // the last plain items of the order, one per CTA, also go out in pieces:
     // the CTAs then run out of work at nearly the same time
-    const int tail = h->step_blocks;
+    const int tail = h->fine ? (int)items : h->step_blocks;
     cudaError_t e = launch_item_order(h->P, h->O, S, split, tail, (int*)h->O.order, dcount, h->stream);
     int n = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&n, dcount, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
