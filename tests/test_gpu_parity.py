@@ -230,3 +230,21 @@ def test_field_stats_watchdog():
     bad.set_field(0, e)
     s, m, n = bad.field_stats(0)
     assert n == 2 and m == 2.5 and abs(s - 6.25) < 1e-12
+
+
+@pytest.mark.parametrize("n,bc", [((16, 12, 20), ("cpml", "periodic", "pec")),
+                                  ((160, 160, 64), ("cpml", "cpml", "cpml")),
+                                  ((4, 4, 300), ("periodic", "periodic", "mur"))],
+                         ids=["few-items", "many-items", "slab-like"])
+def test_split_calls_are_bit_identical(n, bc):
+    """The step hands out its work items through a counter that runs on
+    across launches (each CTA's first two items by position, the rest by
+    ticket, small grids entirely in pieces).  Stepping in many short calls
+    must give the same bits as one long call, on a grid with fewer work items
+    than CTA slots, one with more, and a long thin one."""
+    w = W.random_box(n=n, bc=bc, seed=21, cpml_cells=4, theta=1.0)
+    st = _state(w, 5)
+    a = run_gpu(w, 24, st)
+    b = run_gpu(w, 24, st, chunks=[1, 1, 1, 5, 1, 15])
+    for c in range(9):
+        assert np.array_equal(a.field(c), b.field(c)), c
