@@ -524,9 +524,13 @@ __global__ void __launch_bounds__(kThreads, 2)
         // periodic seams that the TMA box cannot wrap
         const bool seam = (P.per[0] && (x0 - 4 < 0 || x0 + kEX - 4 > P.N[0])) ||
                           (P.per[1] && (y0 - 1 < 0 || y0 + kEY - 1 > P.N[1]));
+        // box entries a valid point or the halo reads: columns x0-2 .. x0+kTX,
+        // rows y0-1 .. y0+kTY, each clipped to one past the grid's last point
+        const int pw = min(kEX - 1, min(x0 + kTX, P.N[0]) - (x0 - 4)) - 1;
+        const int ph = min(kEY - 1, min(y0 + kTY, P.N[1]) - (y0 - 1)) + 1;
         auto patch = [&](StageBuf& sb, int k, int sax) {
-            for (int u = tid; u < kEY * kEX; u += kThreads) {
-                const int jj = u / kEX, ii = u % kEX;
+            for (int u = tid; u < pw * ph; u += kThreads) {
+                const int jj = u / pw, ii = 2 + u % pw;
                 const int x = x0 - 4 + ii, y = y0 - 1 + jj;
                 if (x >= 0 && x < P.N[0] && y >= 0 && y < P.N[1]) continue;
                 const int xw = wrap_or_out(P, 0, x), yw = wrap_or_out(P, 1, y);
