@@ -375,7 +375,7 @@ def run_ours(args, ws, rank, local):
 def run_adjoint(args):
     """Gradient of |X(f0)|^2 with respect to every cell's eps_r and lambda_L
     on the 256 x 128 x 64 adjoint CPW by the discrete adjoint (forward with
-    checkpoints every 256 steps, per-segment recompute, transposed steps),
+    checkpoints every --adjoint-segment steps (256), per-segment recompute, transposed steps),
     timed whole, against the plain step on the same grid."""
     import time
     import torch
@@ -392,11 +392,12 @@ def run_adjoint(args):
     g = tf.Grid.from_workload(w)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    J, ge, gl = g.adjoint(args.adjoint_steps, 0, 0, segment=256)
+    J, ge, gl = g.adjoint(args.adjoint_steps, 0, 0, segment=args.adjoint_segment)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3
     per = ms / args.adjoint_steps
-    return {"workload": w.name, "steps": args.adjoint_steps, "segment": 256, "ms": ms, "ms_per_step": per,
+    return {"workload": w.name, "steps": args.adjoint_steps, "segment": args.adjoint_segment, "ms": ms,
+            "ms_per_step": per,
             "plain_ms_per_step": plain, "vs_plain_step": per / plain,
             "gcell_updates_per_s": w.ncells * args.adjoint_steps / (ms * 1e-3) / 1e9,
             "objective": J, "grad_eps_absmax": float(ge.abs().max()), "grad_lambda_absmax": float(gl.abs().max()),
@@ -610,6 +611,7 @@ def main(argv=None):
     ap.add_argument("--study-workload", choices=("cpw", "cpw_large"), default="cpw")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--adjoint-steps", type=int, default=8000)
+    ap.add_argument("--adjoint-segment", type=int, default=256, help="steps between the adjoint's checkpoints")
     args = ap.parse_args(argv)
     ws, rank, local = dist_env()
     if args.warmup < 3:
