@@ -550,7 +550,8 @@ def run_precision_study(args):
     line = {"study": "fp32 fused step vs fp64 stepper", "workload": w.name, "steps": args.fp64_study,
             "field_rel_l2_vs_peak": rows, "probe_spectrum_rel_l2": spec,
             "fp32_gcell_updates_per_s": cells * args.fp64_study / t32 / 1e9,
-            "fp64_gcell_updates_per_s": cells * args.fp64_study / t64 / 1e9}
+            "fp64_gcell_updates_per_s": cells * args.fp64_study / t64 / 1e9,
+            "fp64_fma_gflops": tf.fp64_fma_rate()}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -608,6 +609,7 @@ def main(argv=None):
     ap.add_argument("--all-configs", action="store_true", help="per-config GPU and oracle numbers, one JSON line")
     ap.add_argument("--large-steps", type=int, default=200)
     ap.add_argument("--fp64-study", type=int, default=0, help="run only the FP32-vs-FP64 study over this many steps")
+    ap.add_argument("--fp64-peak", action="store_true", help="measure only the FP64 FMA rate (one JSON line)")
     ap.add_argument("--study-workload", choices=("cpw", "cpw_large"), default="cpw")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--adjoint-steps", type=int, default=8000)
@@ -618,6 +620,12 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.fp64_peak:
+        from paper_2305_13419_gb300 import twofluid as tf
+        rates = [tf.fp64_fma_rate() for _ in range(3)]
+        print(json.dumps({"measure": "FP64 FMA rate (library kernel of independent FMA chains)", "unit": "GFLOP/s",
+                          "runs": rates, "best": max(rates)}), flush=True)
+        return 0
     if args.fp64_study > 0:
         return run_precision_study(args)
     if args.all_configs:

@@ -306,6 +306,18 @@ tf_status tf64_read_field(tf64_handle h, int comp, double* dst);
 tf_status tf64_read_probe_dft(tf64_handle h, int id, double* re, double* im);
 tf_status tf64_get_time(tf64_handle h, int64_t* n, double* dt);
 
+/* The FP64 FMA rate of the current device, the arithmetic ceiling of the
+ * FP64 stepper (a measurement for the FP32-vs-FP64 study; the paper has no
+ * counterpart).  Runs a kernel of independent FP64 FMA chains, `iters`
+ * rounds per thread, on `stream` (a cudaStream_t, NULL for the default
+ * stream), timed with CUDA events after one untimed run, and writes GFLOP/s
+ * (2 per FMA) to *gflops.  dev_scratch: device memory of at least
+ * tf64_fma_rate_scratch() bytes (caller-owned; overwritten).  Synchronises
+ * the stream.  TF_EINVAL on a null pointer or iters < 1, TF_ENOMEM if the
+ * scratch is too small, TF_ECUDA on a CUDA error. */
+size_t tf64_fma_rate_scratch(void);
+tf_status tf64_fma_rate(void* dev_scratch, size_t bytes, int iters, void* stream, double* gflops);
+
 const char* tf_strerror(tf_status s);
 
 #ifdef __cplusplus

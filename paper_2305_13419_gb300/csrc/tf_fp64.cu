@@ -33,10 +33,10 @@ constexpr double kC0d = 299792458.0, kMu0d = 1.25663706212e-6, kEps0d = 8.854187
 struct G64 {
     int n[3], N[3], per[3], bc[3], L[3], edge_rule;
     long long np;
-    double d[3], dt, theta, murM;
+    double d[3], id[3], dt, theta, murM;   // id: 1 / d
     double *E[3], *B[3], *J[3], *Eold[3];
     double *psiB[3][3], *psiE[3][3];
-    double *epsE[3], *sigE[3], *kapE[3], *muF[3];
+    double *caE[3], *cbE[3], *kapE[3], *imuF[3];   // theta-scheme coefficients of step 3, kappa, 1 / mu_face
     double *pbE[3], *pcE[3], *pbB[3], *pcB[3];
     const double *eps_c, *mu_c, *kap_c, *sig_c;
 };
@@ -118,23 +118,28 @@ __global__ void k64_coeffs(G64 g) {
             }
             mu = kMu0d * sm / 2.0;
         }
-        g.epsE[c][t] = eps;
-        g.sigE[c][t] = sig;
+        // step 3: E' = ca E + cb (curl H - J), ca = (1 - (1-theta) s) / (1 + theta s),
+        // cb = (dt / eps) / (1 + theta s), s = sigma dt / eps (formed once, not per step)
+        const double sd = sig * g.dt / eps, den = 1.0 + g.theta * sd;
+        g.caE[c][t] = (1.0 - (1.0 - g.theta) * sd) / den;
+        g.cbE[c][t] = g.dt / eps / den;
         g.kapE[c][t] = kap;
-        g.muF[c][t] = mu;
+        g.imuF[c][t] = 1.0 / mu;
     }
 }
 
 __device__ __forceinline__ double dE(const G64& g, int e, int a, const int p[3]) {
     int q[3] = {p[0], p[1], p[2]};
     q[a] = up(g, a, p[a]);
-    return (g.E[e][ix(g, q[0], q[1], q[2])] - g.E[e][ix(g, p[0], p[1], p[2])]) / g.d[a];
+    return (g.E[e][ix(g, q[0], q[1], q[2])] - g.E[e][ix(g, p[0], p[1], p[2])]) * g.id[a];
 }
 __device__ __forceinline__ double dH(const G64& g, int h, int a, const int p[3]) {
     int q[3] = {p[0], p[1], p[2]};
     q[a] = dn(g, a, p[a]);
     const long long i0 = ix(g, p[0], p[1], p[2]), i1 = ix(g, q[0], q[1], q[2]);
-    return (g.B[h][i0] / g.muF[h][i0] - g.B[h][i1] / g.muF[h][i1]) / g.d[a];
+    // the two products rounded on their own (no fused multiply-add), so that
+    // equal neighbours give an exact zero as the oracle's divisions do
+    return (__dmul_rn(g.B[h][i0], g.imuF[h][i0]) - __dmul_rn(g.B[h][i1], g.imuF[h][i1])) * g.id[a];
 }
 
 // steps 1 and 5: B -= dt/2 curl E (with psi_B)
@@ -193,9 +198,7 @@ __global__ void k64_E(G64 g) {
             if (g.psiE[c][a]) v += g.psiE[c][a][t];
             r += sgn(c, a) * v;
         }
-        const double eps = g.epsE[c][t], s = g.sigE[c][t] * g.dt / eps;
-        const double e = g.E[c][t];
-        g.E[c][t] = (e * (1.0 - (1.0 - g.theta) * s) + g.dt / eps * (r - g.J[c][t])) / (1.0 + g.theta * s);
+        g.E[c][t] = g.caE[c][t] * g.E[c][t] + g.cbE[c][t] * (r - g.J[c][t]);
     }
 }
 
@@ -350,6 +353,7 @@ tf_status tf64_create(const tf_grid_desc* d, void* ws, size_t bytes, tf64_handle
         g.bc[a] = d->bc[a].kind;
         g.L[a] = d->bc[a].kind == TF_BC_CPML ? d->bc[a].cpml_cells : 0;
         g.d[a] = h[a];
+        g.id[a] = 1.0 / h[a];
     }
     g.np = L.np;
     g.edge_rule = d->edge_rule;
@@ -362,8 +366,8 @@ tf_status tf64_create(const tf_grid_desc* d, void* ws, size_t bytes, tf64_handle
     for (int k = 0; k < 3; ++k) {
         g.E[k] = (double*)take(fb); g.B[k] = (double*)take(fb); g.J[k] = (double*)take(fb);
         g.Eold[k] = (double*)take(fb);
-        g.epsE[k] = (double*)take(fb); g.sigE[k] = (double*)take(fb); g.kapE[k] = (double*)take(fb);
-        g.muF[k] = (double*)take(fb);
+        g.caE[k] = (double*)take(fb); g.cbE[k] = (double*)take(fb); g.kapE[k] = (double*)take(fb);
+        g.imuF[k] = (double*)take(fb);
     }
     for (int a = 0; a < 3; ++a)
         for (int k = 0; k < 3; ++k) {
@@ -589,3 +593,56 @@ tf_status tf64_get_time(tf64_handle h, int64_t* n, double* dt) {
 }
 
 }  // extern "C"
+
+namespace {
+constexpr int kFmaChains = 8, kFmaThreads = 256, kFmaBlocksPerSm = 4;
+// FP64 FMA throughput: kFmaChains independent chains per thread, the results
+// written out so that none of the work can be dropped
+__global__ void __launch_bounds__(kFmaThreads) k64_fma_rate(double* out, int iters, double a, double b) {
+    const int t = blockIdx.x * kFmaThreads + threadIdx.x;
+    double x[kFmaChains];
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) x[c] = 1e-3 * (t + c);
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int c = 0; c < kFmaChains; ++c) x[c] = fma(x[c], a, b);
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c) s += x[c];
+    out[t] = s;
+}
+}  // namespace
+
+extern "C" size_t tf64_fma_rate_scratch(void) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sizeof(double) * (size_t)sms * kFmaBlocksPerSm * kFmaThreads;
+}
+
+extern "C" tf_status tf64_fma_rate(void* dev_scratch, size_t bytes, int iters, void* stream, double* gflops) {
+    if (!dev_scratch || !gflops || iters < 1) return TF_EINVAL;
+    int dev = 0, sms = 0;
+    C64(cudaGetDevice(&dev));
+    C64(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * kFmaBlocksPerSm;
+    if (bytes < sizeof(double) * (size_t)blocks * kFmaThreads) return TF_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    C64(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return TF_ECUDA;
+    }
+    k64_fma_rate<<<blocks, kFmaThreads, 0, st>>>((double*)dev_scratch, iters, 0.999999, 1e-7);   // warm-up
+    cudaEventRecord(e0, st);
+    k64_fma_rate<<<blocks, kFmaThreads, 0, st>>>((double*)dev_scratch, iters, 0.999999, 1e-7);
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    const cudaError_t e = cudaEventSynchronize(e1) == cudaSuccess ? cudaEventElapsedTime(&ms, e0, e1) : cudaErrorUnknown;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess || !(ms > 0.f)) return TF_ECUDA;
+    *gflops = 2.0 * kFmaChains * (double)iters * blocks * kFmaThreads / (ms * 1e-3) / 1e9;
+    return TF_OK;
+}

@@ -30,7 +30,7 @@ EXPORTS = ["tf_workspace_size", "tf_create", "tf_destroy", "tf_storage_dims", "t
            "tf_checkpoint_save", "tf_checkpoint_load", "tf_adjoint_scratch_size", "tf_adjoint_run", "tf_batch_step",
            "tf64_workspace_size", "tf64_create", "tf64_destroy", "tf64_set_materials", "tf64_set_field",
            "tf64_add_source", "tf64_add_probe", "tf64_step", "tf64_sync", "tf64_read_field", "tf64_read_probe_dft",
-           "tf64_get_time"]
+           "tf64_get_time", "tf64_fma_rate_scratch", "tf64_fma_rate"]
 
 
 class TFError(RuntimeError):
@@ -106,12 +106,15 @@ def load(build_if_missing: bool = True):
                        ("tf64_add_probe", [vp, C.c_int, ip, dp, C.c_int, C.c_int64, ip]),
                        ("tf64_step", [vp, C.c_int64]), ("tf64_sync", [vp]), ("tf64_read_field", [vp, C.c_int, vp]),
                        ("tf64_read_probe_dft", [vp, C.c_int, dp, dp]),
-                       ("tf64_get_time", [vp, C.POINTER(C.c_int64), dp])):
+                       ("tf64_get_time", [vp, C.POINTER(C.c_int64), dp]),
+                       ("tf64_fma_rate", [vp, C.c_size_t, C.c_int, vp, dp])):
         fn = getattr(L, name)
         fn.restype = st
         fn.argtypes = args
     L.tf64_workspace_size.restype = C.c_size_t
     L.tf64_workspace_size.argtypes = [C.POINTER(tf_grid_desc)]
+    L.tf64_fma_rate_scratch.restype = C.c_size_t
+    L.tf64_fma_rate_scratch.argtypes = []
     L.tf_strerror.restype = C.c_char_p
     L.tf_strerror.argtypes = [C.c_int]
     _lib = L
@@ -186,6 +189,22 @@ def tf_field_stats_noalloc(field, nx_pts, ny_pts, nz_pts, pitch, scale=1.0, stre
                                          float(scale), C.byref(s), C.byref(m), C.byref(n),
                                          C.c_void_p(stream)), "tf_field_stats_noalloc")
     return s.value, m.value, int(n.value)
+
+
+def fp64_fma_rate(iters: int = 20000, device=None, stream=None) -> float:
+    """FP64 FMA rate of the device in GFLOP/s (the FP64 stepper's arithmetic
+    ceiling), measured by the library's FMA-chain kernel."""
+    import torch
+    dev = torch.device(device if device is not None else "cuda")
+    n = load().tf64_fma_rate_scratch()
+    if n == 0:
+        raise TFError(TF_ECUDA, "tf64_fma_rate_scratch")
+    scratch = torch.empty(int(n), dtype=torch.uint8, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    g = C.c_double()
+    _check(load().tf64_fma_rate(C.c_void_p(scratch.data_ptr()), int(n), int(iters), C.c_void_p(st.cuda_stream),
+                                C.byref(g)), "tf64_fma_rate")
+    return g.value
 
 
 class Grid64:

@@ -57,3 +57,19 @@ def test_fp64_gpu_sources_and_probes():
     for p in range(3):
         X, Y = g.probe_dft(p), o.probe_dft(p, len(w.probes[p].freqs))
         assert np.max(np.abs(X - Y)) <= 1e-12 * np.max(np.abs(Y))
+
+
+def test_fp64_fma_rate_measures_and_rejects_bad_calls():
+    """The FP64 FMA-rate probe (the FP64 stepper's arithmetic ceiling)
+    returns a finite positive rate and rejects bad arguments."""
+    import ctypes as C
+    import torch
+    from paper_2305_13419_gb300 import twofluid as tf
+    r = tf.fp64_fma_rate(iters=2000)
+    assert np.isfinite(r) and r > 0
+    n = tf.load().tf64_fma_rate_scratch()
+    buf = torch.empty(int(n), dtype=torch.uint8, device="cuda")
+    g = C.c_double()
+    assert tf.load().tf64_fma_rate(C.c_void_p(buf.data_ptr()), int(n) - 8, 10, None, C.byref(g)) == tf.TF_ENOMEM
+    assert tf.load().tf64_fma_rate(C.c_void_p(buf.data_ptr()), int(n), 0, None, C.byref(g)) == tf.TF_EINVAL
+    assert tf.load().tf64_fma_rate(None, int(n), 10, None, C.byref(g)) == tf.TF_EINVAL
