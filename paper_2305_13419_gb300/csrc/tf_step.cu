@@ -28,10 +28,14 @@
 // accesses; its arithmetic uses the packed FP32x2 add / sub / mul / fma of
 // the sm_100 family.  E, B and psi_B ping-pong between two arrays (the other
 // tiles only ever read the old ones); Js and psi_E are owned by one thread
-// and update in place.  Work items (tile, z chunk) come from an atomic
-// counter through an order that hands out the slow items first; the grid
-// fills every SM twice.  Periodic x / y seams, which a TMA box cannot wrap,
-// are patched from global memory after the box lands.
+// and update in place.  Work items (tile, z chunk) are handed out through an
+// order that puts the slow items first, the others z chunk by z chunk and
+// the last ones in short pieces; each CTA starts with two items by position
+// and draws the rest from an atomic counter; the grid fills every SM twice.
+// The CPML profile coefficients of an item sit in a shared table filled one
+// item ahead.  The first CTAs also add E^n at the probe points to the
+// running DFTs while their ring fills.  Periodic x / y seams, which a TMA
+// box cannot wrap, are patched from global memory after the box lands.
 //
 // x / y walls are per-point masks, the low z wall a plane mask; the CPML
 // memory of the staged axis comes from shared memory, that of any further
