@@ -438,6 +438,33 @@ def run_batch(args, plain_gcells):
     return out
 
 
+def run_batch_singles(args):
+    """The batch's grids stepped one at a time (each alone on the GPU): the
+    per-grid rate that the batched stepping is compared with."""
+    import time
+    import torch
+    from paper_2305_13419_gb300 import twofluid as tf
+    from paper_2305_13419_gb300 import workloads as W
+    rows, cells, secs = [], 0, 0.0
+    for w in W.cpw_batch()[:args.batch_singles]:
+        g = tf.Grid.from_workload(w)
+        g.step(20)
+        g.sync()
+        t0 = time.perf_counter()
+        g.step(args.batch_steps)
+        g.sync()
+        dt = (time.perf_counter() - t0) / args.batch_steps
+        rows.append({"grid": w.name, "ms_per_step": dt * 1e3, "gcell_updates_per_s": w.ncells / dt / 1e9})
+        cells += w.ncells
+        secs += dt
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    print(json.dumps({"measure": "batch grids stepped one at a time", "steps": args.batch_steps, "grids": rows,
+                      "aggregate_gcell_updates_per_s": cells / secs / 1e9}), flush=True)
+    return 0
+
+
 def run_config(w, steps, warmup=5):
     """GPU throughput of the plain step on one workload: the whole step timed
     with CUDA events on the handle's stream, and the step kernel's
@@ -610,6 +637,8 @@ def main(argv=None):
     ap.add_argument("--large-steps", type=int, default=200)
     ap.add_argument("--fp64-study", type=int, default=0, help="run only the FP32-vs-FP64 study over this many steps")
     ap.add_argument("--fp64-peak", action="store_true", help="measure only the FP64 FMA rate (one JSON line)")
+    ap.add_argument("--batch-singles", type=int, default=0,
+                    help="time only the first N grids of the batch one at a time (one JSON line)")
     ap.add_argument("--study-workload", choices=("cpw", "cpw_large"), default="cpw")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--adjoint-steps", type=int, default=8000)
@@ -620,6 +649,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.batch_singles > 0:
+        return run_batch_singles(args)
     if args.fp64_peak:
         from paper_2305_13419_gb300 import twofluid as tf
         rates = [tf.fp64_fma_rate() for _ in range(3)]
