@@ -1,8 +1,10 @@
-"""Benchmark: Gcell-updates/s of the two-fluid Yee step on the CPW resonator
-(512 x 256 x 128 cells, CPML 12, London + Ohmic films, soft source, two
-64-frequency probe DFTs), plus the HBM roofline fraction of the dominant
-kernel, an end-to-end number through the C ABI with host buffers, and the
-FP64 CPU oracle on the same workload as the baseline.
+"""Benchmark: Gcell-updates/s of the two-fluid Yee step on the large CPW
+resonator (1024 x 512 x 256 cells = 134 M, CPML 16, lambda_L = 4 cells,
+London + Ohmic films, soft source, two 64-frequency probe DFTs), plus the
+HBM roofline fraction of the dominant kernel, an end-to-end number through
+the C ABI with host buffers, the FP64 CPU oracle on a block of the same
+workload as the baseline, and the other workloads (512 x 256 x 128 CPW,
+4 x 4 x 2048 slab, adjoint, batch) beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -75,7 +77,13 @@ def sum_over_ranks(dist, value: float, device=None) -> float:
 def replica_seed(rank: int) -> int:
     """Replica r draws its own sigma map (a different resonator variant)."""
     from paper_2305_13419_gb300 import workloads as W
-    return W.BASE_SEED + 2 + 1000 * rank
+    return W.BASE_SEED + 5 + 1000 * rank
+
+
+def headline_workload(rank: int = 0):
+    """The 1024 x 512 x 256 CPW (the largest single-GPU configuration)."""
+    from paper_2305_13419_gb300 import workloads as W
+    return W.cpw_large(seed=replica_seed(rank))
 
 
 def aggregate(cells_per_rank, steps, max_ms, world):
@@ -200,9 +208,9 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """dram bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources; else None."""
+def ncu_traffic(kernel: str, workload: str):
+    """dram bytes per launch of `kernel` on `workload` from the committed ncu
+    summary, if it was taken on the current kernel sources; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -212,8 +220,8 @@ def ncu_traffic(kernel: str):
         return None
     if d.get("source_hash") != source_hash():
         return None
-    k = d.get("kernels", {}).get(kernel)
-    return None if k is None else k.get("dram_bytes_per_launch_fullsize")
+    k = d.get("kernels", {}).get(kernel, {}).get(workload)
+    return None if k is None else k.get("dram_bytes_per_launch")
 
 
 def hbm_peak():
@@ -246,15 +254,16 @@ def cpu_baseline(w, budget_s=10.0):
             "sample": f"{w.name}: {n} FP64 oracle steps after one untimed step ({el:.1f} s)"}
 
 
-def reference_sample_workload():
-    """Bounded sample of the CPW workload for the oracle arm: a 128 x 128 x 64
-    cell block cut from it around the in-port / resonator gap at the film
-    plane, closed with PEC walls."""
+def large_block(nx=256, ny=256, nz=128):
+    """A cell block of the 1024 x 512 x 256 CPW cut around the in-port /
+    resonator gap at the film plane, closed with PEC walls: the bounded
+    sample the FP64 oracle steps on the host cores."""
     from paper_2305_13419_gb300 import workloads as W
-    w = W.cpw()
-    sl = (slice(0, 64), slice(64, 192), slice(48, 176))
-    return W.Workload(name="cpw-512x256x128[48:176,64:192,0:64]", n=(128, 128, 64), d=w.d, theta=w.theta,
-                      bc=("pec", "pec", "pec"), eps_r=np.ascontiguousarray(w.eps_r[sl]),
+    w = headline_workload()
+    x0, y0 = 256 - nx // 2 + 128, 256 - ny // 2
+    sl = (slice(0, nz), slice(y0, y0 + ny), slice(x0, x0 + nx))
+    return W.Workload(name=f"cpw-1024x512x256[{x0}:{x0 + nx},{y0}:{y0 + ny},0:{nz}]", n=(nx, ny, nz), d=w.d,
+                      theta=w.theta, bc=("pec", "pec", "pec"), eps_r=np.ascontiguousarray(w.eps_r[sl]),
                       mu_r=np.ascontiguousarray(w.mu_r[sl]), lambda_L=np.ascontiguousarray(w.lambda_L[sl]),
                       sigma=np.ascontiguousarray(w.sigma[sl]), courant=w.courant)
 
@@ -263,7 +272,7 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return 0
     from oracle import stepper
-    w = reference_sample_workload()
+    w = large_block(128, 128, 64)
     threads = stepper.set_threads(os.cpu_count() or 1)
     g = stepper.Grid.from_workload(w)
     g.step(args.warmup)
@@ -271,7 +280,7 @@ def run_reference(args, ws, rank):
     g.step(args.steps)
     el = time.perf_counter() - t0
     v = w.ncells * args.steps / el / 1e9
-    sample = f"{w.name}: {args.steps} FP64 oracle steps on a 1/16 block of the workload"
+    sample = f"{w.name}: {args.steps} FP64 oracle steps on a 1/128 block of the workload"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -283,12 +292,27 @@ def run_reference(args, ws, rank):
 
 
 def config_block(state_bytes=None):
-    c = {"workload": "cpw-512x256x128: CPW resonator, CPML 12, lambda_L = 3 cells, sigma_n ~ U[0,1e6] S/m, "
+    c = {"workload": "cpw-1024x512x256: CPW resonator, CPML 16, lambda_L = 4 cells, sigma_n ~ U[0,1e6] S/m, "
                      "theta = 1, Courant 0.95, +/- Gaussian-sine port source, 2 probes x 64-frequency DFT",
-         "cells": 512 * 256 * 128, "parallelism": "replicas (independent resonator per GPU)"}
+         "cells": 1024 * 512 * 256, "parallelism": "replicas (independent resonator per GPU)"}
     if state_bytes:
         c["l2"] = f"inputs larger than L2: {state_bytes / 2**20:.0f} MiB of fields and maps per step > 129 MiB"
     return c
+
+
+def roofline_of(w, N, kt, kernel="k_step"):
+    """Roofline of the fused step kernel: its algorithmic bytes per launch
+    over its mean event-timed launch duration, against the measured HBM peak."""
+    ab = algorithmic_bytes(w, N)
+    peak, peak_kind = hbm_peak()
+    step_s = kt["step"][0] * 1e-3
+    achieved = ab["step"] / step_s / 1e9
+    return ab, {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(kernel, w.name), "algorithmic_bytes": ab["step"],
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "dense_equivalent_GBps": ab["dense_equivalent"] / step_s / 1e9,
+                "effective_frac_dense_equivalent": ab["dense_equivalent"] / step_s / 1e9 / peak,
+                "kernel_ms": {k: v[0] for k, v in kt.items()}}
 
 
 # ------------------------------------------------------------------ our arm
@@ -300,43 +324,31 @@ def run_ours(args, ws, rank, local):
     dist = init_dist(ws, "nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = W.cpw(seed=replica_seed(rank))
+    w = headline_workload(rank)
     g = tf.Grid.from_workload(w)
     N = g.N
-    ab = algorithmic_bytes(w, N)
-    state_bytes = (9 + 3) * 4 * ab["points"]
 
-    # device-timed throughput: inputs resident in HBM, K steps between barriers
+    # device-timed throughput: inputs resident in HBM, K steps between
+    # barriers; CUDA events on the grid's stream around every launch, so the
+    # whole run and the kernel's own durations come from the same launches
     g.step(args.warmup)
     g.sync()
     torch.cuda.synchronize()
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(dist)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        start.record(g.stream)
-        g.step(args.steps)
-        stop.record(g.stream)
+        kt, ms = g.step_timed(args.steps, with_total=True)
         torch.cuda.synchronize()
     barrier(dist)
-    ms = start.elapsed_time(stop)
     g.sync()
     ms_max = max_over_ranks(dist, ms, dev)
     value = aggregate(w.ncells, args.steps, ms_max, ws)
-
-    # per-kernel durations over the same number of steps (events around each launch)
-    kt = g.step_timed(args.steps)
-    g.sync()
-    peak, peak_kind = hbm_peak()
-    step_s = kt["step"][0] * 1e-3
-    achieved = ab["step"] / step_s / 1e9
-    traffic = ncu_traffic("k_step")
-    roof = {"bound": "hbm", "kernel": "k_step", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": ab["step"],
-            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-            "dense_equivalent_GBps": ab["dense_equivalent"] / step_s / 1e9,
-            "kernel_ms": {k: v[0] for k, v in kt.items()}}
-    launches_per_step = len(kt)  # probe DFT + fused step
+    ab, roof = roofline_of(w, N, kt)
+    state_bytes = (9 + 3) * 4 * ab["points"]
+    launches_per_step = len(kt)
+    g.close()
+    del g
+    torch.cuda.empty_cache()
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -345,19 +357,19 @@ def run_ours(args, ws, rank, local):
 
     base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(w, budget_s=args.cpu_budget)
+        base = cpu_baseline(large_block(), budget_s=args.cpu_budget)
+        base["sample"] += " (a 256 x 256 x 128 block of the 1024 x 512 x 256 workload, PEC-closed)"
 
     adj = batch = extra = None
-    if rank == 0 and (not args.no_adjoint or not args.no_batch or not args.no_configs):
-        g.close()
-        del g
+    del w
+    if rank == 0 and not args.no_configs:
+        extra = {"cpw-512x256x128": run_config(W.cpw(), args.cpw_steps, 20),
+                 "slab-4x4x2048": run_config(W.slab(), 4000, 50)}
+    plain_small = extra["cpw-512x256x128"]["gcell_updates_per_s"] if extra else None
     if rank == 0 and not args.no_adjoint:
         adj = run_adjoint(args)
     if rank == 0 and not args.no_batch:
-        batch = run_batch(args, value / ws)
-    if rank == 0 and not args.no_configs:
-        extra = {"slab": run_config(W.slab(), 4000, 50),
-                 "large": run_config(W.cpw_large(), args.large_steps, 5)}
+        batch = run_batch(args, plain_small or value / ws)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -466,31 +478,24 @@ def run_batch_singles(args):
 
 
 def run_config(w, steps, warmup=5):
-    """GPU throughput of the plain step on one workload: the whole step timed
-    with CUDA events on the handle's stream, and the step kernel's
-    algorithmic bytes over its own event-timed launches."""
+    """GPU throughput of the plain step on one workload: the whole run and
+    the step kernel's own launches timed with CUDA events on the handle's
+    stream over the same launches; the kernel's algorithmic bytes over its
+    mean launch time give the roofline fraction."""
     import torch
     from paper_2305_13419_gb300 import twofluid as tf
     g = tf.Grid.from_workload(w)
     g.step(warmup)
     g.sync()
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    start.record(g.stream)
-    g.step(steps)
-    stop.record(g.stream)
-    torch.cuda.synchronize()
-    ms = start.elapsed_time(stop) / steps
-    kt = g.step_timed(steps)
+    kt, ms = g.step_timed(steps, with_total=True)
     g.sync()
-    ab = algorithmic_bytes(w, g.N)
+    _, roof = roofline_of(w, g.N, kt)
     g.close()
-    peak, _ = hbm_peak()
-    achieved = ab["step"] / (kt["step"][0] * 1e-3) / 1e9
-    return {"workload": w.name, "cells": w.ncells, "steps": steps, "ms_per_step": ms,
-            "gcell_updates_per_s": w.ncells / (ms * 1e-3) / 1e9,
-            "roofline": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "algorithmic_bytes": ab["step"]}}
+    del g
+    torch.cuda.empty_cache()
+    return {"workload": w.name, "cells": w.ncells, "steps": steps, "ms_per_step": ms / steps,
+            "gcell_updates_per_s": w.ncells * steps / (ms * 1e-3) / 1e9, "roofline": roof}
 
 
 def run_all_configs(args):
@@ -624,8 +629,9 @@ def run_e2e(args, w, dev):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--cpw-steps", type=int, default=2000, help="steps of the 512 x 256 x 128 CPW line")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -169,8 +169,14 @@ tf_status tf_step(tf_handle h, int64_t nsteps);
  * kernel kind k and launches[k] the number of launches, for k = 0 a separate
  * probe DFT kernel (no longer launched: the fused step adds E^n at the probes
  * to their DFTs while its ring fills, so launches[0] stays 0) and k = 1 the
- * fused step (arrays of nkinds <= 2 entries). */
-tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds);
+ * fused step (arrays of nkinds <= 2 entries).  total_ms (may be NULL)
+ * receives the event time from the first launch's start to the last
+ * launch's end: the same launches' whole-run time.  Up to 4096 steps are
+ * enqueued before the call waits on the stream (longer runs wait once per
+ * 4096 steps, and total_ms then sums those batches).  Host memory for the
+ * events is allocated per call (TF_ENOMEM if that fails). */
+tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds,
+                        double* total_ms);
 
 /* Advance n independent grids by nsteps steps each (the batched workload:
  * many resonator variants at once).  The grids advance together, one step
@@ -224,7 +230,9 @@ tf_status tf_checkpoint_load(tf_handle h, const void* src, size_t bytes, int on_
  *   forward, saving a checkpoint every `segment` steps into the scratch,
  *   then walks the segments backwards: each is recomputed from its
  *   checkpoint with E kept at every level, and the transposed step runs back
- *   through it, summing per-edge gradients in FP64.
+ *   through it, summing per-edge gradients in FP64.  The adjoint's seed is
+ *   scaled by a power of two to O(1) (and the gradients scaled back), so the
+ *   FP32 adjoint state stays in FP32's normal range for any source size.
  *   scratch   caller-owned device memory of at least tf_adjoint_scratch_size
  *             bytes (checkpoints, one segment of E history, the adjoint
  *             state, the gradient sums); TF_ENOMEM if smaller;

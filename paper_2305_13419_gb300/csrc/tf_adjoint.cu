@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(kAX * kAY) k_adj_edges(Params P, AdjState A, S
 
 // per cell: dJ/d eps_r and dJ/d lambda_L from the per-edge sums, with the
 // weights of the edge rule (eps: mean of 4 cells; kt: mean over the 4 cells
-// or over the superconducting ones)
-__global__ void __launch_bounds__(256) k_adj_cells(Params P, AdjState A, float dt_c0, float* g_eps,
-                                                          float* g_lam) {
+// or over the superconducting ones); `unscale` undoes the seed's scaling
+__global__ void __launch_bounds__(256) k_adj_cells(Params P, AdjState A, float dt_c0, double unscale, float* g_eps,
+                                                   float* g_lam) {
     const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
     const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
     if (t >= nc) return;
@@ -196,11 +196,11 @@ __global__ void __launch_bounds__(256) k_adj_cells(Params P, AdjState A, float d
                 }
             }
     }
-    g_eps[t] = (float)ge;
+    g_eps[t] = (float)(ge * unscale);
     float gl = 0.f;
     if (kc > 0.f) {   // kt = (c0 dt / lambda)^2 / mu_r: d kt / d lambda = -2 kt / lambda
         const float lam = dt_c0 / sqrtf(kc * __ldg(P.mu + m));
-        gl = (float)(gk * (-2.0 * (double)kc / (double)lam));
+        gl = (float)(gk * unscale * (-2.0 * (double)kc / (double)lam));
     }
     g_lam[t] = gl;
 }
@@ -234,10 +234,10 @@ cudaError_t launch_adjoint_step(const Params& P, const AdjState& A, const Source
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0, float* g_eps, float* g_lam,
-                                 cudaStream_t stream) {
+cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0, double unscale, float* g_eps,
+                                 float* g_lam, cudaStream_t stream) {
     const long long nc = (long long)P.n[0] * P.n[1] * P.n[2];
-    k_adj_cells<<<(unsigned)((nc + 255) / 256), 256, 0, stream>>>(P, A, dt_c0, g_eps, g_lam);
+    k_adj_cells<<<(unsigned)((nc + 255) / 256), 256, 0, stream>>>(P, A, dt_c0, unscale, g_eps, g_lam);
     return cudaGetLastError();
 }
 

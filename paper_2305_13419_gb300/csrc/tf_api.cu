@@ -611,35 +611,41 @@ tf_status tf_batch_step(const tf_handle* hs, int n, int64_t nsteps) {
     return TF_OK;
 }
 
-tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds) {
+tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds,
+                        double* total_ms) {
     if (!h || nsteps < 0 || !kernel_ms || !launches || nkinds < 1 || nkinds > 2) return TF_EINVAL;
     for (int k = 0; k < nkinds; ++k) { kernel_ms[k] = 0.0; launches[k] = 0; }
+    if (total_ms) *total_ms = 0.0;
     if (nsteps == 0) return TF_OK;
     if (!h->primed) {
         TF_CUDA(launch_prime(h->P, h->stream));
         h->primed = 1;
     }
-    constexpr int kRing = 64;
-    cudaEvent_t ev[kRing][3];
-    int created = 0;
+    // events for up to kBatch steps are enqueued before the stream is waited
+    // on, so a run of up to kBatch steps goes out without a pause
+    constexpr int64_t kBatch = 4096;
+    const int64_t ring = nsteps < kBatch ? nsteps : kBatch;
+    cudaEvent_t(*ev)[3] = (cudaEvent_t(*)[3])calloc((size_t)ring, sizeof(cudaEvent_t[3]));
+    if (!ev) return TF_ENOMEM;
     tf_status rc = TF_OK;
-    for (; created < kRing; ++created) {
-        bool ok = true;
+    for (int64_t s = 0; s < ring && rc == TF_OK; ++s)
         for (int m = 0; m < 3; ++m)
-            if (cudaEventCreate(&ev[created][m]) != cudaSuccess) ok = false;
-        if (!ok) { rc = TF_ECUDA; ++created; break; }
-    }
+            if (cudaEventCreate(&ev[s][m]) != cudaSuccess) {
+                ev[s][m] = nullptr;
+                rc = TF_ECUDA;
+                break;
+            }
     const int has[2] = {0, 1};   // the probes are sampled inside the step: no launch of their own
     Sources S;
     fill_sources(h, S);
-    if (refresh_order(h, S) != cudaSuccess) rc = TF_ECUDA;
+    if (rc == TF_OK && refresh_order(h, S) != cudaSuccess) rc = TF_ECUDA;
     int64_t done = 0;
     while (rc == TF_OK && done < nsteps) {
-        const int m = (int)((nsteps - done) < kRing ? (nsteps - done) : kRing);
-        for (int s = 0; s < m && rc == TF_OK; ++s)
+        const int64_t m = (nsteps - done) < ring ? (nsteps - done) : ring;
+        for (int64_t s = 0; s < m && rc == TF_OK; ++s)
             if (launch_one_step(h, S, ev[s]) != cudaSuccess) rc = TF_ECUDA;
         if (rc != TF_OK || cudaStreamSynchronize(h->stream) != cudaSuccess) { rc = TF_ECUDA; break; }
-        for (int s = 0; s < m; ++s)
+        for (int64_t s = 0; s < m && rc == TF_OK; ++s)
             for (int k = 0; k < nkinds; ++k) {
                 if (!has[k]) continue;
                 float ms = 0.f;
@@ -647,10 +653,17 @@ tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t*
                 kernel_ms[k] += ms;
                 launches[k] += 1;
             }
+        if (rc == TF_OK && total_ms) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[0][0], ev[m - 1][2]) != cudaSuccess) rc = TF_ECUDA;
+            *total_ms += ms;
+        }
         done += m;
     }
-    for (int s = 0; s < created && s < kRing; ++s)
-        for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[s][k]);
+    for (int64_t s = 0; s < ring; ++s)
+        for (int k = 0; k < 3; ++k)
+            if (ev[s][k]) cudaEventDestroy(ev[s][k]);
+    free(ev);
     for (int k = 0; k < nkinds; ++k)
         if (launches[k]) kernel_ms[k] /= (double)launches[k];
     return rc;
@@ -895,6 +908,13 @@ tf_status tf_adjoint_run(tf_handle h, int64_t nsteps, int probe, int freq_index,
     const double xr = re[freq_index], xi = im[freq_index];
     *J = xr * xr + xi * xi;
     const double f = h->freqs[probe][freq_index];
+    // The adjoint is linear in its seed dJ/dE^n = 2 dt Re(conj(X) w^n), whose
+    // size is 2 dt |X| (1e-32 for a 1 V/m source on the CPW grids): scaled by
+    // a power of two to O(1), the FP32 adjoint state stays out of FP32's
+    // subnormal range while it decays into the CPML; the FP64 gradient sums
+    // are scaled back once at the end (exact: a power of two).
+    const double seed = 2.0 * h->dt * sqrt(*J);
+    const double seed_scale = seed > 0.0 && isfinite(seed) ? ldexp(1.0, -ilogb(seed)) : 1.0;
     // adjoint state and gradient sums start at zero
     TF_CUDA(cudaMemsetAsync(sc + A.off_state, 0, A.bytes - A.off_state, h->stream));
     AdjState S{};
@@ -957,14 +977,15 @@ tf_status tf_adjoint_run(tf_handle h, int64_t nsteps, int probe, int freq_index,
                 double ph = f * h->dt * (double)n;
                 ph -= floor(ph);
                 const double ang = 6.283185307179586476925286766559 * ph;
-                st.probe_src = (float)(2.0 * h->dt * (xr * cos(ang) - xi * sin(ang)));
+                st.probe_src = (float)(seed_scale * 2.0 * h->dt * (xr * cos(ang) - xi * sin(ang)));
             }
             const double t1 = (double)(n + 1) * h->dt;
             for (int q = 0; q < h->nsrc; ++q) src.amp[q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
             TF_CUDA(launch_adjoint_step(h->P, S, src, st, h->stream));
         }
     }
-    TF_CUDA(launch_adjoint_cells(h->P, S, (float)(kC0 * h->dt), grad_eps, grad_lambda, h->stream));
+    TF_CUDA(launch_adjoint_cells(h->P, S, (float)(kC0 * h->dt), 1.0 / seed_scale, grad_eps, grad_lambda,
+                                 h->stream));
     // leave the handle in the state the forward run reached
     if ((rc = tf_checkpoint_load(h, sc + A.off_ck + A.nseg * A.ck, A.ck, 1)) != TF_OK) return rc;
     TF_CUDA(cudaStreamSynchronize(h->stream));

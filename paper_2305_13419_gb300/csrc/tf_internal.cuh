@@ -298,8 +298,8 @@ cudaError_t launch_adjoint_step(const Params& P, const AdjState& A, const Source
                                 cudaStream_t stream);
 // copy three float arrays of n elements (n a multiple of 4, 16-byte aligned)
 cudaError_t launch_copy3(float* const dst[3], float* const src[3], long long n, cudaStream_t stream);
-cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0, float* g_eps, float* g_lam,
-                                 cudaStream_t stream);
+cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0, double unscale, float* g_eps,
+                                 float* g_lam, cudaStream_t stream);
 
 // order in which k_step hands out its work items (items needing the full plane loop first)
 cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int tail, int* order,

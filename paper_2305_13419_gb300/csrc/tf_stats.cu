@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_planes(const float* f, i
     unsigned long long nf = 0;
     const int npts = n0 * n1;
     for (int t = threadIdx.x; t < npts; t += kStatThreads) {
-        const float v = p[(t / n0) * pitch + (t % n0)];
+        // 64-bit offset: a caller's row pitch may make pitch * n1 exceed 2^31
+        const float v = p[(long long)(t / n0) * pitch + (t % n0)];
         if (!isfinite(v)) {
             ++nf;
         } else {

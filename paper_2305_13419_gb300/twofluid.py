@@ -84,7 +84,7 @@ def load(build_if_missing: bool = True):
                                           C.c_double, ip]),
                        ("tf_add_probe", [vp, C.c_int, ip, dp, C.c_int, C.c_int64, ip]),
                        ("tf_step", [vp, C.c_int64]), ("tf_sync", [vp]),
-                       ("tf_step_timed", [vp, C.c_int64, dp, C.POINTER(C.c_int64), C.c_int]),
+                       ("tf_step_timed", [vp, C.c_int64, dp, C.POINTER(C.c_int64), C.c_int, dp]),
                        ("tf_read_probe_dft", [vp, C.c_int, dp, dp]),
                        ("tf_read_probe_series", [vp, C.c_int, dp, C.c_int64]),
                        ("tf_read_field", [vp, C.c_int, fp, C.c_int]),
@@ -185,6 +185,10 @@ def tf_field_stats_noalloc(field, nx_pts, ny_pts, nz_pts, pitch, scale=1.0, stre
     pointer of a CUDA tensor); returns (sum of squares, max |v|, non-finite)."""
     s, m, n = C.c_double(), C.c_double(), C.c_int64()
     ptr = int(field.data_ptr()) if hasattr(field, "data_ptr") else int(field)
+    if stream is None and getattr(field, "is_cuda", False):
+        # the stream the tensor's producers run on, not the legacy default stream
+        import torch
+        stream = torch.cuda.current_stream(field.device).cuda_stream
     _check(load().tf_field_stats_noalloc(C.c_void_p(ptr), int(nx_pts), int(ny_pts), int(nz_pts), int(pitch),
                                          float(scale), C.byref(s), C.byref(m), C.byref(n),
                                          C.c_void_p(stream)), "tf_field_stats_noalloc")
@@ -424,13 +428,16 @@ class Grid:
     def sync(self):
         tf_sync(self.h)
 
-    def step_timed(self, nsteps: int):
-        """Advance like step(); returns {kernel: (mean ms per launch, launches)}."""
+    def step_timed(self, nsteps: int, with_total: bool = False):
+        """Advance like step(); returns {kernel: (mean ms per launch, launches)}
+        (and, with_total, also the whole run's event time in ms)."""
         ms = (C.c_double * 2)()
         cnt = (C.c_int64 * 2)()
-        _check(load().tf_step_timed(self.h, int(nsteps), ms, cnt, 2), "tf_step_timed")
+        tot = C.c_double()
+        _check(load().tf_step_timed(self.h, int(nsteps), ms, cnt, 2, C.byref(tot)), "tf_step_timed")
         names = ("probe", "step")
-        return {names[k]: (ms[k], int(cnt[k])) for k in range(2) if cnt[k]}
+        kt = {names[k]: (ms[k], int(cnt[k])) for k in range(2) if cnt[k]}
+        return (kt, tot.value) if with_total else kt
 
     @property
     def level(self) -> int:

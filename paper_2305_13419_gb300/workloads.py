@@ -355,6 +355,68 @@ def cpw_batch(count: int = 64, seed: int = BASE_SEED + 3, nsteps: int = 8000, si
     return out
 
 
+# A 1-D column is a 1 x 1 x nz grid, periodic in x and y: a uniform plane
+# wave has no x or y differences, so the transverse spacing does not enter
+# the fields.  It is set to 1 mm so that the 3-D Courant number of the
+# column is its 1-D one along z (the paper's 1-D runs quote the 1-D number).
+COLUMN_DXY = 1.0e-3
+
+
+def skin_column(sigma: float, f: float, depth: float, lam: float = 400e-9, d: float = 10e-9,
+                courant_1d: float = 0.9, n_vac: int = 100, z_src: int = 50, spinup_periods: int = 4,
+                window_periods: int = 2) -> Workload:
+    """Skin-depth run of Sec. 4.1 / Table 1 as a 1-D column: vacuum for
+    z < n_vac, a superconductor (London depth `lam`, conductivity `sigma`)
+    above, dz = 10 nm, dt = 0.9 dz / c.  An x-polarised soft source at z_src
+    emits a continuous sine of frequency f; after `spinup_periods` periods the
+    probes' DFTs at f run over `window_periods` whole periods (the steady
+    state's amplitude).  `depth` (metres, the caller's expected skin depth)
+    sets the probe spacing and the column length: probes on Ex at the
+    interface and at depths of 1/2, 1 and 2 `depth` inside; the
+    superconductor is 25 depths thick (at least 40 cells) and ends on a wall
+    of the Mur kind, as does the vacuum end."""
+    m = max(1, int(round(depth / d)))
+    nz = n_vac + max(25 * m, 40) + 1
+    dt = courant_1d * d / C0
+    per = 1.0 / (f * dt)                        # steps per period
+    n0 = int(round(spinup_periods * per))
+    nsteps = n0 + int(round(window_periods * per))
+    eps = np.ones((nz, 1, 1), np.float32)
+    mu = np.ones_like(eps)
+    lam_map = np.zeros_like(eps)
+    sig = np.zeros_like(eps)
+    lam_map[n_vac:] = lam
+    sig[n_vac:] = sigma
+    src = Source(comp=0, lo=(0, 0, z_src), hi=(1, 1, z_src + 1), amp=1.0, kind=SRC_SIN, f=f)
+    prb = [Probe(comp=0, p=(0, 0, n_vac + z), freqs=np.array([f]), n0=n0) for z in (0, m // 2, m, 2 * m)]
+    return Workload(name=f"skin-column-sigma{sigma:g}-f{f:g}", n=(1, 1, nz), d=(COLUMN_DXY, COLUMN_DXY, d),
+                    theta=1.0, bc=("periodic", "periodic", "mur"), eps_r=eps, mu_r=mu, lambda_L=lam_map, sigma=sig,
+                    dt=dt, sources=[src], probes=prb, nsteps=nsteps,
+                    notes=f"probe depths 0, {m // 2}, {m}, {2 * m} cells; window [{n0}, {nsteps})")
+
+
+def reflection_column(sigma: float, vacuum: bool = False, nz: int = 4480, d: float = 20e-9, z_if: int = 350,
+                      z_probe: int = 340, nsteps: int = 15800, tw: float = 0.25e-15) -> Workload:
+    """Reflection run of Sec. 4.2 as a 1-D column: 4480 cells of dz = 20 nm,
+    dt = 0.95 dz / c, a superconductor (lambda_L = 100 nm, conductivity
+    `sigma`) from 7 um, Mur walls; a short Gaussian soft source (tw = 0.25 fs,
+    t0 = 4 tw) on Ex at 100 nm covers 0 - 1000 THz; probe at 6.8 um with 64
+    frequencies over 20 - 1000 THz.  `vacuum=True` is the companion run
+    without the superconductor (the incident wave)."""
+    eps = np.ones((nz, 1, 1), np.float32)
+    mu = np.ones_like(eps)
+    lam = np.zeros_like(eps)
+    sig = np.zeros_like(eps)
+    if not vacuum:
+        lam[z_if:] = 100e-9
+        sig[z_if:] = sigma
+    src = Source(comp=0, lo=(0, 0, 5), hi=(1, 1, 6), amp=1.0, kind=SRC_GAUSS, t0=4 * tw, tw=tw)
+    prb = [Probe(comp=0, p=(0, 0, z_probe), freqs=np.linspace(20e12, 1000e12, 64), n0=0)]
+    return Workload(name=f"reflection-column-sigma{sigma:g}{'-vacuum' if vacuum else ''}", n=(1, 1, nz),
+                    d=(COLUMN_DXY, COLUMN_DXY, d), theta=1.0, bc=("periodic", "periodic", "mur"), eps_r=eps,
+                    mu_r=mu, lambda_L=lam, sigma=sig, dt=0.95 * d / C0, sources=[src], probes=prb, nsteps=nsteps)
+
+
 def random_box(n=(9, 7, 11), bc=("periodic", "periodic", "periodic"), seed: int = 1,
                d=(10e-9, 12e-9, 8e-9), courant: float = 0.9, theta: float = 0.5,
                sc_fraction: float = 0.5, lam_range=(30e-9, 60e-9), sigma_range=(0.0, 1e6),

@@ -287,3 +287,43 @@ def test_qfit_on_oracle_damped_oscillation():
     res = qfit.fit(g.probe_dft(0), fr, dt, n0, N)
     assert abs(res["Q"] / q_exact - 1) < 1e-6
     assert abs(res["f0"] / (om / (2 * math.pi)) - 1) < 1e-9
+
+
+# ------------------------------------------------ CW skin depth (Table 1)
+TABLE1 = [(float(r[0]), float(r[1]), float(r[4]) * 1e-9, float(r[5])) for r in read_table("table1_skin_depth.txt")]
+
+
+def cw_skin_depth(g, w):
+    """Table 1's measure, delta = z0 / ln(E0 / E_z0): E0 the steady-state
+    amplitude (DFT over whole periods) at the interface, E_z0 the one at the
+    probe one expected depth inside."""
+    X = [abs(g.probe_dft(p, 1)[0]) for p in range(len(w.probes))]
+    z0 = (w.probes[2].p[2] - w.probes[0].p[2]) * w.d[2]
+    return z0 / math.log(X[0] / X[2])
+
+
+CW_RUNS = {1e12: (2, 1), 100e12: (40, 2)}   # spin-up and window periods per frequency
+
+
+@pytest.mark.parametrize("sigma,f", [(s, f) for s in (0.0, 1e4, 1e7) for f in (1e12, 100e12)])
+def test_cw_skin_depth_table1(sigma, f):
+    """Sec. 4.1, Table 1, by the paper's own method (continuous sine, steady
+    state, delta = z0 / ln(E0 / E_z0)) on a 1-D column with dz = 10 nm and
+    CFL 0.9, lambda = 400 nm: the oracle reproduces the paper's computed
+    column within 1 % where the skin depth spans more than two cells, and
+    Eq. skin within 1.2 % (0.8 % of it is the near-cut-off case sigma = 0 at
+    100 THz, whose computed value the paper also prints 0.7 % above theory;
+    the 1.6-cell case sigma = 1e7 at 100 THz, printed as 13 nm, is
+    compared with theory only, within 3 %)."""
+    delta_th = float(theory.skin_depth(2 * math.pi * f, sigma=sigma, lam=400e-9))
+    sp, wp = CW_RUNS[f]
+    w = W.skin_column(sigma, f, delta_th, spinup_periods=sp, window_periods=wp)
+    g = stepper.Grid.from_workload(w)
+    g.step(w.nsteps)
+    delta = cw_skin_depth(g, w)
+    row = [r for r in TABLE1 if r[0] == sigma and r[1] == f][0]
+    if delta_th > 2 * w.d[2]:
+        assert abs(delta / row[2] - 1) < 1e-2, (delta, row)
+        assert abs(delta / delta_th - 1) < 1.2e-2, (delta, delta_th)
+    else:
+        assert abs(delta / delta_th - 1) < 3e-2, (delta, delta_th)

@@ -65,3 +65,23 @@ def test_noalloc_rejects_more_planes_than_its_scratch():
     with pytest.raises(tf.TFError) as ex:
         tf.tf_field_stats_noalloc(dev, 2, 2, 4097, 2, 1.0)
     assert ex.value.status == tf.TF_EINVAL
+
+
+def test_noalloc_rows_wider_than_the_field():
+    """A caller's array whose rows are padded (pitch > nx_pts) with garbage
+    past the x end: only the first nx_pts values of each row count, twice in
+    a row, and the same numbers as numpy on the unpadded values."""
+    from paper_2305_13419_gb300 import twofluid as tf
+    rng = np.random.default_rng(5)
+    nx, ny, nz, pitch = 37, 23, 19, 160
+    vals = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    padded = np.full((nz, ny, pitch), np.nan, np.float32)   # padding would count as non-finite
+    padded[:, :, :nx] = vals
+    dev = torch.from_numpy(padded).cuda()
+    torch.cuda.synchronize()
+    ref = (float(np.sum(vals.astype(np.float64) ** 2)), float(np.max(np.abs(vals))), 0)
+    for _ in range(2):
+        got = tf.tf_field_stats_noalloc(dev, nx, ny, nz, pitch, 2.0)
+        assert abs(got[0] - 4.0 * ref[0]) <= 1e-12 * 4.0 * ref[0], (ref, got)
+        assert got[1] == 2.0 * ref[1], (ref, got)
+        assert got[2] == 0, got
