@@ -326,6 +326,7 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local)
     w = headline_workload(rank)
     g = tf.Grid.from_workload(w)
+    g.set_two_step(args.two_step != "off")
     N = g.N
 
     # device-timed throughput: inputs resident in HBM, K steps between
@@ -363,8 +364,9 @@ def run_ours(args, ws, rank, local):
     adj = batch = extra = None
     del w
     if rank == 0 and not args.no_configs:
-        extra = {"cpw-512x256x128": run_config(W.cpw(), args.cpw_steps, 20),
-                 "slab-4x4x2048": run_config(W.slab(), 4000, 50)}
+        two = args.two_step != "off"
+        extra = {"cpw-512x256x128": run_config(W.cpw(), args.cpw_steps, 20, two),
+                 "slab-4x4x2048": run_config(W.slab(), 4000, 50, two)}
     plain_small = extra["cpw-512x256x128"]["gcell_updates_per_s"] if extra else None
     if rank == 0 and not args.no_adjoint:
         adj = run_adjoint(args)
@@ -477,7 +479,7 @@ def run_batch_singles(args):
     return 0
 
 
-def run_config(w, steps, warmup=5):
+def run_config(w, steps, warmup=5, two_step=True):
     """GPU throughput of the plain step on one workload: the whole run and
     the step kernel's own launches timed with CUDA events on the handle's
     stream over the same launches; the kernel's algorithmic bytes over its
@@ -485,6 +487,7 @@ def run_config(w, steps, warmup=5):
     import torch
     from paper_2305_13419_gb300 import twofluid as tf
     g = tf.Grid.from_workload(w)
+    g.set_two_step(two_step)
     g.step(warmup)
     g.sync()
     torch.cuda.synchronize()
@@ -632,6 +635,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--cpw-steps", type=int, default=2000, help="steps of the 512 x 256 x 128 CPW line")
+    ap.add_argument("--two-step", choices=("auto", "off"), default="auto",
+                    help="two steps per pass on the interior box where the grid has one (auto) or single steps only")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

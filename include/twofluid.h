@@ -169,14 +169,34 @@ tf_status tf_step(tf_handle h, int64_t nsteps);
  * kernel kind k and launches[k] the number of launches, for k = 0 a separate
  * probe DFT kernel (no longer launched: the fused step adds E^n at the probes
  * to their DFTs while its ring fills, so launches[0] stays 0) and k = 1 the
- * fused step (arrays of nkinds <= 2 entries).  total_ms (may be NULL)
+ * fused step and k = 2 the two-step kernel of tf_set_two_step (arrays of
+ * nkinds <= 3 entries; a two-step pass counts one launch of kind 2 and two
+ * of kind 1).  total_ms (may be NULL)
  * receives the event time from the first launch's start to the last
  * launch's end: the same launches' whole-run time.  Up to 4096 steps are
  * enqueued before the call waits on the stream (longer runs wait once per
- * 4096 steps, and total_ms then sums those batches).  Host memory for the
+ * 4096 launch groups, and total_ms then sums those batches).  Host memory for the
  * events is allocated per call (TF_ENOMEM if that fails). */
 tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds,
                         double* total_ms);
+
+/* Temporal blocking: two time steps of Algorithm 1 (Sec. 3) per pass over
+ * the memory.  tf_step advances a grid two steps at a time where it can: a
+ * two-step kernel moves the interior box -- the tiles and planes whose
+ * points, with a two-point halo, lie off the walls, off the Mur planes and
+ * outside the CPML slabs -- from level n to n + 2 in one pass, and the
+ * single-step kernel moves the rest of the grid twice.  The results are the
+ * same bits as single steps.  It is used when the box is not empty, mu is
+ * uniform (tf_set_materials) and it is enabled; an odd step count ends with a
+ * single step.
+ *   tf_set_two_step  enable (1, the default) or disable (0) it for this
+ *                    handle (TF_EINVAL for other values); a tuning switch,
+ *                    results do not change.
+ *   tf_two_step_box  the box in storage points, [lo, hi) per axis (all zero
+ *                    when the geometry has none), and in *active (may be
+ *                    NULL) whether tf_step uses it. */
+tf_status tf_set_two_step(tf_handle h, int enable);
+tf_status tf_two_step_box(tf_handle h, int lo[3], int hi[3], int* active);
 
 /* Advance n independent grids by nsteps steps each (the batched workload:
  * many resonator variants at once).  The grids advance together, one step

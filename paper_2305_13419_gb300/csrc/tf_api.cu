@@ -24,7 +24,8 @@ struct Layout {
     int ncpml_axes;         // axes with a CPML (6 psi arrays each)
     int ntx, nty, nch, kend; // fused-step tiles, z chunks, planes iterated
     size_t off_fields, off_maps, off_psi, off_prof, off_zero, off_probe, off_series, off_scratch,
-        off_tiles, off_order, off_stats, off_coef, off_misc, bytes;
+        off_tiles, off_order, off_order_s, off_order_t, off_stats, off_coef, off_misc, bytes;
+    long long max_s, max_t;   // capacity of the shell and two-step work lists
     long long scratch_floats;
 };
 
@@ -54,7 +55,7 @@ tf_status validate(const tf_grid_desc* d) {
     if (d->max_probes < 0 || d->max_probes > TF_MAX_PROBES || d->series_capacity < 0) return TF_EINVAL;
     const long long pts = (long long)(n[0] + 1) * (n[1] + 1) * (n[2] + 1);
     if (pts > (1LL << 40)) return TF_EINVAL;
-    // work-item descriptors hold 16 bits of tile index and 12 bits of plane
+    // work-item descriptors hold 20 bits of tile index and 20 bits of plane
     const long long tx = (n[0] + 1 + kSX - 1) / kSX, ty = (n[1] + 1 + kSY - 1) / kSY;
     if (tx * ty > kMaxTiles || n[2] + 1 > kMaxPlanes) return TF_ENOTSUP;
     return TF_OK;
@@ -81,9 +82,9 @@ Layout layout_of(const tf_grid_desc* d) {
     L.nch = (L.kend + kChunk - 1) / kChunk;
     const size_t fbytes = align_up(sizeof(float) * (size_t)L.total);
     size_t o = 0;
-    L.off_fields = o; o += 15 * fbytes;   // E, B (two buffers each), Js
+    L.off_fields = o; o += kFieldArrays * fbytes;   // E, B, Js in three buffers
     L.off_maps = o;   o += 4 * fbytes;
-    L.off_psi = o;    o += 6 * (size_t)L.ncpml_axes * fbytes;   // per axis: psi_B pair x 2 buffers, psi_E pair
+    L.off_psi = o;    o += kPsiGroup * (size_t)L.ncpml_axes * fbytes;   // per axis: psi_B pair x 3 buffers, psi_E pair
     L.off_coef = o;   o += 9 * fbytes;                             // per-point ca, cb, cj of each E component
     L.off_prof = o;
     for (int a = 0; a < 3; ++a) o += 4 * align_up(sizeof(float) * (size_t)L.N[a]);
@@ -93,7 +94,13 @@ Layout layout_of(const tf_grid_desc* d) {
     L.scratch_floats = 4 * L.ncell > L.ndense ? 4 * L.ncell : L.ndense;
     L.off_scratch = o; o += align_up(sizeof(float) * (size_t)L.scratch_floats);
     L.off_tiles = o;  o += align_up(sizeof(float4) * (size_t)L.ntx * L.nty * L.N[2]);
-    L.off_order = o;  o += align_up(sizeof(int) * (size_t)L.ntx * L.nty * L.nch * ((kChunk + kSub - 1) / kSub));
+    L.off_order = o;  o += align_up(sizeof(long long) * (size_t)L.ntx * L.nty * L.nch * ((kChunk + kSub - 1) / kSub));
+    // shell list: the chunks of every tile, two more per tile where the
+    // two-step box cuts them, each chunk in pieces at most
+    L.max_s = (long long)L.ntx * L.nty * (L.nch + 2) * ((kChunk + kSub - 1) / kSub);
+    L.off_order_s = o; o += align_up(sizeof(long long) * (size_t)L.max_s);
+    L.max_t = (long long)L.ntx * L.nty * (L.N[2] / kTBLenMax + 1);
+    L.off_order_t = o; o += align_up(sizeof(long long) * (size_t)L.max_t);
     L.off_stats = o;  o += align_up(sizeof(StatPartial) * (size_t)(L.N[2] + 1));
     L.off_misc = o;   o += kAlign;
     L.bytes = o;
@@ -118,13 +125,27 @@ double waveform(const SrcHost& s, double t) {
 }  // namespace
 
 struct tf_ctx {
-    alignas(128) unsigned char tmap[3][128];   // TMA descriptors: E box, B box, psi_B box
+    // TMA descriptors: the single-step E box, B box and psi_B box; the two-step E box and B box
+    alignas(128) unsigned char tmap[5][128];
     tf_grid_desc desc;
     Layout L;
-    Params P;
-    StepOut O;
-    int parity;         // which of the two E / B buffers holds the current state
+    Params P;           // the current state (buffer cur) ...
+    StepOut O;          // ... and the next one (buffer nxt): the single-step launch
+    float* fE[kFieldBuffers][3];   // the field arrays of each buffer
+    float* fB[kFieldBuffers][3];
+    float* fJ[kFieldBuffers][3];
+    float* fPB[kFieldBuffers][3][3];   // psi_B [buffer][component][axis]
+    int cur, nxt;       // buffers of the current and the next state (the third one is scratch)
     int step_blocks;
+    int slots, slots2;  // resident CTAs of the single- and two-step kernels on the device
+    // two-step passes: the interior box (tiles [tx0, tx1) x [ty0, ty1), planes [tz0, tz1))
+    int box_ok;         // the geometry has a box (two-step passes also need uniform mu)
+    int tx0, tx1, ty0, ty1, tz0, tz1;
+    int nitems_s, blocks_s, nitems_t, blocks_t;
+    unsigned long long* ctr_t;
+    unsigned long long base_t;
+    int two_step_on;    // two-step passes allowed (tf_set_two_step; on by default)
+    int ppos[TF_MAX_PROBES][3];   // probe points (storage coordinates)
     Probes R;
     cudaStream_t stream;
     double dt;
@@ -141,6 +162,71 @@ struct tf_ctx {
     SrcHost src[TF_MAX_SOURCES];
     double freqs[TF_MAX_PROBES][TF_MAX_FREQS];
 };
+
+namespace {
+
+// Params / StepOut of a step from buffer `from` to buffer `to`
+void bind(const tf_ctx* h, int from, int to, Params& P, StepOut& O) {
+    for (int c = 0; c < 3; ++c) {
+        P.E[c] = h->fE[from][c];
+        P.B[c] = h->fB[from][c];
+        P.J[c] = h->fJ[from][c];
+        O.E[c] = h->fE[to][c];
+        O.B[c] = h->fB[to][c];
+        O.J[c] = h->fJ[to][c];
+        for (int a = 0; a < 3; ++a) {
+            P.psiB[c][a] = h->fPB[from][c][a];
+            O.psiB[c][a] = h->fPB[to][c][a];
+        }
+    }
+    O.ecur = 9 * from;
+    O.bcur = 9 * from + 3;
+    O.psib_cur = psib_index(from);
+}
+
+// the counter of a work list moved once per item past the 2G handed out by
+// position, and once more (the fetch that came back empty) in every CTA that
+// had a second item
+unsigned long long counter_advance(long long ni, long long g) {
+    return (unsigned long long)((ni > 2 * g ? ni - 2 * g : 0) + (ni - g < 0 ? 0 : ni - g > g ? g : ni - g));
+}
+
+// The interior box of the two-step kernel.  Every point that kernel forms
+// (its tiles plus a two-point halo: x0-2 .. x0+33, y0-2 .. y0+16, planes
+// kz0-2 .. kz1) must lie off the walls and off the Mur planes (points 2 ..
+// n-2 of a walled axis) and outside the CPML slabs (cells L .. n-L-1); on a
+// periodic axis its TMA boxes (x0-4 .. x0+35, y0-2 .. y0+17, planes kz0-2 ..
+// kz1+1) must not wrap.  Tiles are those of the single-step kernel.
+void interior_box(tf_ctx* h) {
+    const Params& P = h->P;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        if (P.per[a]) {
+            lo[a] = 0;
+            hi[a] = P.N[a];
+        } else {
+            lo[a] = P.L[a] > 2 ? P.L[a] : 2;
+            hi[a] = P.n[a] - (P.L[a] > 1 ? P.L[a] : 1);
+        }
+    }
+    // x: x0 - 2 >= lo (periodic: x0 - 4 >= 0), x0 + 34 <= hi (periodic: x0 + 36 <= N)
+    const int xl = P.per[0] ? 4 : lo[0] + 2, xh = P.per[0] ? hi[0] - 36 : hi[0] - 34;
+    h->tx0 = (xl + kSX - 1) / kSX;
+    h->tx1 = xh >= 0 ? xh / kSX + 1 : 0;
+    // y: y0 - 2 >= lo, y0 + 17 <= hi (periodic: y0 + 18 <= N)
+    const int yl = lo[1] + 2, yh = P.per[1] ? hi[1] - 18 : hi[1] - 17;
+    h->ty0 = (yl + kSY - 1) / kSY;
+    h->ty1 = yh >= 0 ? yh / kSY + 1 : 0;
+    // z: kz0 - 2 >= lo, kz1 + 1 <= hi (periodic: kz1 + 2 <= N)
+    h->tz0 = lo[2] + 2;
+    h->tz1 = P.per[2] ? hi[2] - 2 : hi[2] - 1;
+    if (h->tx1 > h->L.ntx) h->tx1 = h->L.ntx;
+    if (h->ty1 > h->L.nty) h->ty1 = h->L.nty;
+    h->box_ok = h->tx1 > h->tx0 && h->ty1 > h->ty0 && h->tz1 - h->tz0 >= 4;
+    if (!h->box_ok) h->tx0 = h->tx1 = h->ty0 = h->ty1 = h->tz0 = h->tz1 = 0;
+}
+
+}  // namespace
 
 #define TF_CUDA(x)                                  \
     do {                                            \
@@ -225,62 +311,63 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
     const size_t fbytes = align_up(sizeof(float) * (size_t)L.total);
     char* base = h->ws;
     StepOut& O = h->O;
-    for (int c = 0; c < 3; ++c) {
-        P.E[c] = (float*)(base + L.off_fields + (0 + c) * fbytes);
-        P.B[c] = (float*)(base + L.off_fields + (3 + c) * fbytes);
-        P.J[c] = (float*)(base + L.off_fields + (6 + c) * fbytes);
-        O.E[c] = (float*)(base + L.off_fields + (9 + c) * fbytes);
-        O.B[c] = (float*)(base + L.off_fields + (12 + c) * fbytes);
-    }
+    for (int b = 0; b < kFieldBuffers; ++b)
+        for (int c = 0; c < 3; ++c) {
+            h->fE[b][c] = (float*)(base + L.off_fields + (size_t)(9 * b + c) * fbytes);
+            h->fB[b][c] = (float*)(base + L.off_fields + (size_t)(9 * b + 3 + c) * fbytes);
+            h->fJ[b][c] = (float*)(base + L.off_fields + (size_t)(9 * b + 6 + c) * fbytes);
+            for (int a = 0; a < 3; ++a) h->fPB[b][c][a] = nullptr;
+        }
     float* maps[4];
     for (int m = 0; m < 4; ++m) maps[m] = (float*)(base + L.off_maps + m * fbytes);
     P.eps = maps[0]; P.sig = maps[1]; P.kap = maps[2]; P.mu = maps[3];
     // psi arrays: per CPML axis a (slot s), with c1 < c2 the two components != a:
-    //   [psiB(c1) buf0, psiB(c2) buf0, psiB(c1) buf1, psiB(c2) buf1, psiE(c1), psiE(c2)]
+    //   [psiB(c1) buf0, psiB(c2) buf0, psiB(c1) buf1, psiB(c2) buf1, psiE(c1), psiE(c2),
+    //    psiB(c1) buf2, psiB(c2) buf2]
     int slot = 0;
     for (int a = 0; a < 3; ++a) {
         O.psi_slot[a] = -1;
-        for (int c = 0; c < 3; ++c) {
-            P.psiB[c][a] = nullptr;
-            P.psiE[c][a] = nullptr;
-            O.psiB[c][a] = nullptr;
-        }
+        for (int c = 0; c < 3; ++c) P.psiE[c][a] = nullptr;
         if (desc->bc[a].kind != TF_BC_CPML) continue;
         O.psi_slot[a] = slot;
         int m = 0;
         for (int c = 0; c < 3; ++c) {
             if (c == a) continue;
-            char* g0 = base + L.off_psi + (size_t)(6 * slot) * fbytes;
-            P.psiB[c][a] = (float*)(g0 + (size_t)(0 + m) * fbytes);
-            O.psiB[c][a] = (float*)(g0 + (size_t)(2 + m) * fbytes);
+            char* g0 = base + L.off_psi + (size_t)(kPsiGroup * slot) * fbytes;
+            for (int b = 0; b < kFieldBuffers; ++b) h->fPB[b][c][a] = (float*)(g0 + (size_t)(psib_index(b) + m) * fbytes);
             P.psiE[c][a] = (float*)(g0 + (size_t)(4 + m) * fbytes);
             ++m;
         }
         ++slot;
     }
-    O.psib_cur = 0;
     for (int c = 0; c < 3; ++c) {
         P.ca[c] = (const float*)(base + L.off_coef + (size_t)(0 + c) * fbytes);
         P.cb[c] = (const float*)(base + L.off_coef + (size_t)(3 + c) * fbytes);
         P.cj[c] = (const float*)(base + L.off_coef + (size_t)(6 + c) * fbytes);
     }
-    O.ecur = 0;
-    O.bcur = 3;
-    h->parity = 0;
+    h->cur = 0;
+    h->nxt = 1;
+    bind(h, h->cur, h->nxt, P, O);
     if ((long long)P.plane * L.N[2] >= (1LL << 31)) { delete h; return TF_ENOTSUP; }   // 32-bit indexing
-    if (make_tensor_map(base + L.off_fields, L.N, L.pitch, fbytes, 15, kEX, kEY, 3, h->tmap[0]) != cudaSuccess ||
-        make_tensor_map(base + L.off_fields, L.N, L.pitch, fbytes, 15, kBX, kBY, 3, h->tmap[1]) != cudaSuccess) {
+    if (make_tensor_map(base + L.off_fields, L.N, L.pitch, fbytes, kFieldArrays, kEX, kEY, 3, h->tmap[0]) !=
+            cudaSuccess ||
+        make_tensor_map(base + L.off_fields, L.N, L.pitch, fbytes, kFieldArrays, kBX, kBY, 3, h->tmap[1]) !=
+            cudaSuccess ||
+        make_tensor_map(base + L.off_fields, L.N, L.pitch, fbytes, kFieldArrays, kT2BoxX, kT2BoxEY, 3,
+                        h->tmap[3]) != cudaSuccess ||
+        make_tensor_map(base + L.off_fields, L.N, L.pitch, fbytes, kFieldArrays, kT2BoxX, kT2BoxBY, 3,
+                        h->tmap[4]) != cudaSuccess) {
         delete h;
         return TF_ECUDA;
     }
-    if (L.ncpml_axes > 0 &&
-        make_tensor_map(base + L.off_psi, L.N, L.pitch, fbytes, 6 * L.ncpml_axes, kBX, kBY, 2, h->tmap[2]) !=
-            cudaSuccess) {
+    if (L.ncpml_axes > 0 && make_tensor_map(base + L.off_psi, L.N, L.pitch, fbytes, kPsiGroup * L.ncpml_axes, kBX,
+                                            kBY, 2, h->tmap[2]) != cudaSuccess) {
         delete h;
         return TF_ECUDA;
     }
+    interior_box(h);
     O.tilemat = (const float4*)(base + L.off_tiles);
-    O.order = (const int*)(base + L.off_order);
+    O.order = (const long long*)(base + L.off_order);
     h->order_dirty = 1;
     O.ntx = L.ntx;
     O.nty = L.nty;
@@ -328,6 +415,9 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
     h->mm = h->status + 4;
     h->fit_out = (double*)(base + L.off_misc + 64);
     O.ctr = (unsigned long long*)(base + L.off_misc + 128);
+    h->ctr_t = (unsigned long long*)(base + L.off_misc + 160);
+    h->base_t = 0;
+    h->two_step_on = 1;
     P.status = h->status;
     {
         int dev = 0, sms = 1;
@@ -337,8 +427,8 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
             return TF_ECUDA;
         }
         const long long items = (long long)L.ntx * L.nty * L.nch;
-        const int per_sm = step_blocks_per_sm();
-        if (per_sm < 1) {
+        const int per_sm = step_blocks_per_sm(), per_sm2 = step2_blocks_per_sm();
+        if (per_sm < 1 || per_sm2 < 1) {
             delete h;
             return TF_ECUDA;
         }
@@ -346,6 +436,8 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
         // grid then leaves SMs to grids stepping on other streams.  A grid
         // with fewer items than slots goes out in kSub-plane pieces.
         const long long slots = (long long)sms * per_sm;
+        h->slots = (int)slots;
+        h->slots2 = sms * per_sm2;
         h->fine = items < slots;
         const long long units = h->fine ? items * ((kChunk + kSub - 1) / kSub) : items;
         long long nb = slots, half = (units + 1) / 2;
@@ -487,6 +579,7 @@ tf_status tf_add_probe(tf_handle h, int comp, const int p[3], const double* freq
     h->R.nfreq[k] = nfreq;
     h->R.comp[k] = comp;
     h->R.q[k] = lin(h->P, p[0], p[1], p[2]);
+    for (int a = 0; a < 3; ++a) h->ppos[k][a] = p[a];
     h->R.n0[k] = n0;
     h->R.n++;
     if (id) *id = k;
@@ -499,28 +592,181 @@ namespace {
 // swap); with `ev` non-null events are recorded before and after the launch
 cudaError_t launch_one_step(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
     cudaStream_t st = h->stream;
-    cudaError_t e = cudaSuccess;
-    if (ev) cudaEventRecord(ev[0], st);
-    if (ev) cudaEventRecord(ev[1], st);
     const double t1 = (double)(h->level + 1) * h->dt;
     for (int q = 0; q < h->nsrc; ++q) S.amp[q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
-    if (e == cudaSuccess) e = launch_step(h->tmap[0], h->P, h->O, S, h->R, h->level, h->step_blocks, st);
-    if (ev) cudaEventRecord(ev[2], st);
-    // the new state is in O's buffers: swap
-    for (int c = 0; c < 3; ++c) {
-        float* t = h->P.E[c]; h->P.E[c] = h->O.E[c]; h->O.E[c] = t;
-        t = h->P.B[c]; h->P.B[c] = h->O.B[c]; h->O.B[c] = t;
-        for (int a = 0; a < 3; ++a) { t = h->P.psiB[c][a]; h->P.psiB[c][a] = h->O.psiB[c][a]; h->O.psiB[c][a] = t; }
-    }
-    h->parity ^= 1;
-    h->O.psib_cur = h->parity ? 2 : 0;
-    h->O.ecur = h->parity ? 9 : 0;
-    h->O.bcur = h->parity ? 12 : 3;
-    // the counter moved once per item past the 2G handed out at the start,
-    // and once more (the fetch that came back empty) in every CTA that used it
-    const long long ni = h->O.nitems, g = h->step_blocks;
-    h->O.base += (unsigned long long)((ni > 2 * g ? ni - 2 * g : 0) + (ni - g < 0 ? 0 : ni - g > g ? g : ni - g));
+    if (ev) cudaEventRecord(ev[0], st);
+    cudaError_t e = launch_step(h->tmap[0], h->P, h->O, S, h->R, h->level, h->step_blocks, st);
+    if (ev) cudaEventRecord(ev[1], st);
+    h->O.base += counter_advance(h->O.nitems, h->step_blocks);
+    // the new state is in the next buffer
+    const int t = h->cur;
+    h->cur = h->nxt;
+    h->nxt = t;
+    bind(h, h->cur, h->nxt, h->P, h->O);
     h->level++;
+    return e;
+}
+
+// two steps: the two-step kernel on the interior box (current -> next
+// buffer, the box's ring and probe points at level n+1 into the third
+// buffer), then the single-step kernel twice on the shell (current -> third
+// -> next buffer).  Events (when ev is non-null): before the two-step
+// launch, between the launches, after the last.
+cudaError_t launch_two_steps(tf_ctx* h, Sources& S, cudaEvent_t* ev) {
+    cudaStream_t st = h->stream;
+    const int x = h->cur, y = h->nxt, z = 3 - h->cur - h->nxt;
+    const double t1 = (double)(h->level + 1) * h->dt, t2 = (double)(h->level + 2) * h->dt;
+    Step2Out O2;
+    for (int c = 0; c < 3; ++c) {
+        O2.E[c] = h->fE[y][c];
+        O2.B[c] = h->fB[y][c];
+        O2.J[c] = h->fJ[y][c];
+        O2.ZE[c] = h->fE[z][c];
+        O2.ZB[c] = h->fB[z][c];
+    }
+    O2.tilemat = h->O.tilemat;
+    O2.ntx = h->L.ntx;
+    O2.nty = h->L.nty;
+    O2.ecur = 9 * x;
+    O2.bcur = 9 * x + 3;
+    O2.lo[0] = h->tx0 * kSX;
+    O2.hi[0] = h->tx1 * kSX;
+    O2.lo[1] = h->ty0 * kSY;
+    O2.hi[1] = h->ty1 * kSY;
+    O2.lo[2] = h->tz0;
+    O2.hi[2] = h->tz1;
+    O2.order = (const long long*)(h->ws + h->L.off_order_t);
+    O2.nitems = h->nitems_t;
+    O2.ctr = h->ctr_t;
+    O2.base = h->base_t;
+    O2.nprobe = h->R.n;
+    for (int p = 0; p < h->R.n; ++p)
+        for (int a = 0; a < 3; ++a) O2.probe[p][a] = h->ppos[p][a];
+    for (int q = 0; q < h->nsrc; ++q) {
+        S.amp[q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
+        O2.amp2[q] = (float)(h->src[q].amp * waveform(h->src[q], t2));
+    }
+    if (ev) cudaEventRecord(ev[0], st);
+    cudaError_t e = launch_step2(h->tmap[3], h->P, O2, S, h->blocks_t, st);
+    h->base_t += counter_advance(h->nitems_t, h->blocks_t);
+    if (ev) cudaEventRecord(ev[1], st);
+    Params P1 = h->P;
+    StepOut O1 = h->O;
+    O1.order = (const long long*)(h->ws + h->L.off_order_s);
+    O1.nitems = h->nitems_s;
+    bind(h, x, z, P1, O1);
+    O1.base = h->O.base;
+    if (e == cudaSuccess) e = launch_step(h->tmap[0], P1, O1, S, h->R, h->level, h->blocks_s, st);
+    h->O.base += counter_advance(h->nitems_s, h->blocks_s);
+    if (ev) cudaEventRecord(ev[2], st);
+    for (int q = 0; q < h->nsrc; ++q) S.amp[q] = O2.amp2[q];
+    bind(h, z, y, P1, O1);
+    O1.base = h->O.base;
+    if (e == cudaSuccess) e = launch_step(h->tmap[0], P1, O1, S, h->R, h->level + 1, h->blocks_s, st);
+    h->O.base += counter_advance(h->nitems_s, h->blocks_s);
+    if (ev) cudaEventRecord(ev[3], st);
+    h->cur = y;
+    h->nxt = x;
+    bind(h, h->cur, h->nxt, h->P, h->O);
+    h->level += 2;
+    return e;
+}
+
+bool two_step(const tf_ctx* h) { return h->two_step_on && h->box_ok && h->P.uniform_mu && h->nitems_t > 0; }
+
+// host copy of the single-step kernel's rule for the items that take its
+// full plane body (used to order the shell list; the kernel decides again)
+bool rare_item(const tf_ctx* h, const Sources& S, int tile, int kz0, int len) {
+    const Params& P = h->P;
+    if (!P.uniform_mu) return true;
+    const int x0 = (tile % h->L.ntx) * kSX, y0 = (tile / h->L.ntx) * kSY;
+    const int kz1 = kz0 + len, ks = (kz0 > 0 || P.per[2]) ? kz0 - 1 : kz0;
+    const int ka = ks < 0 ? 0 : ks, kb = kz1 - 1;
+    const bool sx = P.L[0] > 0 && (x0 - 1 < P.L[0] || x0 + kSX - 1 >= P.n[0] - P.L[0]);
+    const bool sy = P.L[1] > 0 && (y0 - 1 < P.L[1] || y0 + kSY - 1 >= P.n[1] - P.L[1]);
+    const bool sz = P.L[2] > 0 && (ka < P.L[2] || kb >= P.n[2] - P.L[2]);
+    if ((int)sx + (int)sy + (int)sz >= 2) return true;
+    if (S.n > 0 && x0 + kSX > S.bb_lo[0] && x0 <= S.bb_hi[0] && y0 + kSY > S.bb_lo[1] && y0 <= S.bb_hi[1]) {
+        const int sk0 = S.bb_lo[2], sk1 = S.bb_hi[2];
+        if (sk1 > sk0 && ((kb >= sk0 && ka < sk1) || (ks < 0 && P.N[2] - 1 >= sk0 && P.N[2] - 1 < sk1))) return true;
+    }
+    const bool mur = P.bc[2] == TF_BC_MUR;
+    return mur && ((ka <= 1 && 1 <= kb) || (ka <= P.n[2] - 1 && P.n[2] - 1 <= kb));
+}
+
+// the work lists of two-step passes, built on the host: the shell (every
+// tile's z chunks outside the box; items that take the full plane body
+// first, the others z chunk by z chunk, the last ones in pieces) and the
+// box (its tiles in kTBLenMax-plane items, z chunk by z chunk)
+cudaError_t build_two_step_lists(tf_ctx* h, const Sources& S) {
+    const Layout& L = h->L;
+    long long* sl = (long long*)malloc(sizeof(long long) * (size_t)L.max_s);
+    long long* fa = (long long*)malloc(sizeof(long long) * (size_t)L.max_s);
+    long long* tl = (long long*)malloc(sizeof(long long) * (size_t)L.max_t);
+    if (!sl || !fa || !tl) {
+        free(sl);
+        free(fa);
+        free(tl);
+        return cudaErrorMemoryAllocation;
+    }
+    long long ns = 0, nf = 0, nt = 0, npieces = 0;
+    for (int pass = 0; pass < 2; ++pass) {   // pass 0 counts the pieces, pass 1 lists them
+        const bool split = pass == 1 && npieces < 8LL * h->slots;
+        for (int kz = 0; kz < L.kend; kz += kChunk) {
+            const int ke = kz + kChunk < L.kend ? kz + kChunk : L.kend;
+            for (int ty = 0; ty < L.nty; ++ty)
+                for (int tx = 0; tx < L.ntx; ++tx) {
+                    const int tile = ty * L.ntx + tx;
+                    const bool in = tx >= h->tx0 && tx < h->tx1 && ty >= h->ty0 && ty < h->ty1;
+                    int lo[2] = {kz, 0}, hi[2] = {ke, 0}, np = 1;
+                    if (in) {   // the chunk minus the box's planes [tz0, tz1)
+                        np = 0;
+                        if (kz < h->tz0) { lo[np] = kz; hi[np] = ke < h->tz0 ? ke : h->tz0; ++np; }
+                        if (ke > h->tz1) { lo[np] = kz > h->tz1 ? kz : h->tz1; hi[np] = ke; ++np; }
+                    }
+                    for (int p = 0; p < np; ++p) {
+                        if (hi[p] <= lo[p]) continue;
+                        if (pass == 0) { ++npieces; continue; }
+                        if (rare_item(h, S, tile, lo[p], hi[p] - lo[p])) {
+                            const int piece = split ? kSub : hi[p] - lo[p];
+                            for (int k = lo[p]; k < hi[p]; k += piece)
+                                sl[ns++] = make_item(tile, k, (hi[p] - k) < piece ? hi[p] - k : piece);
+                        } else {
+                            fa[nf++] = make_item(tile, lo[p], hi[p] - lo[p]);
+                        }
+                    }
+                }
+        }
+    }
+    // the last plain items, one per CTA slot, go out in kSub-plane pieces
+    const long long cut = nf > h->slots ? nf - h->slots : 0;
+    for (long long i = 0; i < cut; ++i) sl[ns++] = fa[i];
+    for (long long i = cut; i < nf; ++i) {
+        const long long d = fa[i];
+        const int tile = item_tile(d), kz0 = item_kz0(d), len = item_len(d);
+        for (int k = kz0; k < kz0 + len; k += kSub)
+            sl[ns++] = make_item(tile, k, (kz0 + len - k) < kSub ? kz0 + len - k : kSub);
+    }
+    for (int kz = h->tz0; kz < h->tz1; kz += kTBLenMax) {
+        const int len = h->tz1 - kz < kTBLenMax ? h->tz1 - kz : kTBLenMax;
+        for (int ty = h->ty0; ty < h->ty1; ++ty)
+            for (int tx = h->tx0; tx < h->tx1; ++tx)
+                tl[nt++] = make_item(ty * L.ntx + tx, kz, len);
+    }
+    cudaError_t e = cudaSuccess;
+    if (ns > 0)
+        e = cudaMemcpyAsync(h->ws + L.off_order_s, sl, sizeof(long long) * (size_t)ns, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && nt > 0)
+        e = cudaMemcpyAsync(h->ws + L.off_order_t, tl, sizeof(long long) * (size_t)nt, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    free(sl);
+    free(fa);
+    free(tl);
+    h->nitems_s = (int)ns;
+    h->nitems_t = (int)nt;
+    const long long hs = (ns + 1) / 2, ht = (nt + 1) / 2;
+    h->blocks_s = (int)(hs < h->slots ? (hs > 0 ? hs : 1) : h->slots);
+    h->blocks_t = (int)(ht < h->slots2 ? (ht > 0 ? ht : 1) : h->slots2);
     return e;
 }
 
@@ -534,12 +780,14 @@ cudaError_t refresh_order(tf_ctx* h, const Sources& S) {
     // the last plain items of the order, one per CTA, also go out in pieces:
     // the CTAs then run out of work at nearly the same time
     const int tail = h->fine ? (int)items : h->step_blocks;
-    cudaError_t e = launch_item_order(h->P, h->O, S, split, tail, (int*)h->O.order, dcount, h->stream);
+    cudaError_t e = launch_item_order(h->P, h->O, S, split, tail, (long long*)h->O.order, dcount, h->stream);
     int n = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&n, dcount, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return e;
     h->O.nitems = n;
+    h->nitems_s = h->nitems_t = 0;
+    if (h->box_ok && h->P.uniform_mu && (e = build_two_step_lists(h, S)) != cudaSuccess) return e;
     h->order_dirty = 0;
     return cudaSuccess;
 }
@@ -571,7 +819,28 @@ tf_status tf_step(tf_handle h, int64_t nsteps) {
     Sources S;
     fill_sources(h, S);
     TF_CUDA(refresh_order(h, S));
-    for (int64_t s = 0; s < nsteps; ++s) TF_CUDA(launch_one_step(h, S, nullptr));
+    int64_t s = 0;
+    if (two_step(h))
+        for (; s + 2 <= nsteps; s += 2) TF_CUDA(launch_two_steps(h, S, nullptr));
+    for (; s < nsteps; ++s) TF_CUDA(launch_one_step(h, S, nullptr));
+    return TF_OK;
+}
+
+tf_status tf_set_two_step(tf_handle h, int enable) {
+    if (!h || (enable != 0 && enable != 1)) return TF_EINVAL;
+    h->two_step_on = enable;
+    return TF_OK;
+}
+
+tf_status tf_two_step_box(tf_handle h, int lo[3], int hi[3], int* active) {
+    if (!h || !lo || !hi) return TF_EINVAL;
+    lo[0] = h->tx0 * kSX;
+    hi[0] = h->tx1 * kSX;
+    lo[1] = h->ty0 * kSY;
+    hi[1] = h->ty1 * kSY;
+    lo[2] = h->tz0;
+    hi[2] = h->tz1;
+    if (active) *active = two_step(h) ? 1 : 0;
     return TF_OK;
 }
 
@@ -613,7 +882,7 @@ tf_status tf_batch_step(const tf_handle* hs, int n, int64_t nsteps) {
 
 tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds,
                         double* total_ms) {
-    if (!h || nsteps < 0 || !kernel_ms || !launches || nkinds < 1 || nkinds > 2) return TF_EINVAL;
+    if (!h || nsteps < 0 || !kernel_ms || !launches || nkinds < 1 || nkinds > 3) return TF_EINVAL;
     for (int k = 0; k < nkinds; ++k) { kernel_ms[k] = 0.0; launches[k] = 0; }
     if (total_ms) *total_ms = 0.0;
     if (nsteps == 0) return TF_OK;
@@ -621,48 +890,62 @@ tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t*
         TF_CUDA(launch_prime(h->P, h->stream));
         h->primed = 1;
     }
-    // events for up to kBatch steps are enqueued before the stream is waited
-    // on, so a run of up to kBatch steps goes out without a pause
+    Sources S;
+    fill_sources(h, S);
+    TF_CUDA(refresh_order(h, S));
+    const bool two = two_step(h);
+    // launch groups: two-step passes (three launches) while two steps remain, then single steps
+    const int64_t ncyc = two ? nsteps / 2 : 0, nunits = ncyc + (nsteps - 2 * ncyc);
+    // events for up to kBatch groups are enqueued before the stream is waited
+    // on, so a run of up to kBatch groups goes out without a pause
     constexpr int64_t kBatch = 4096;
-    const int64_t ring = nsteps < kBatch ? nsteps : kBatch;
-    cudaEvent_t(*ev)[3] = (cudaEvent_t(*)[3])calloc((size_t)ring, sizeof(cudaEvent_t[3]));
+    const int64_t ring = nunits < kBatch ? nunits : kBatch;
+    cudaEvent_t(*ev)[4] = (cudaEvent_t(*)[4])calloc((size_t)ring, sizeof(cudaEvent_t[4]));
     if (!ev) return TF_ENOMEM;
     tf_status rc = TF_OK;
-    for (int64_t s = 0; s < ring && rc == TF_OK; ++s)
-        for (int m = 0; m < 3; ++m)
-            if (cudaEventCreate(&ev[s][m]) != cudaSuccess) {
-                ev[s][m] = nullptr;
+    for (int64_t u = 0; u < ring && rc == TF_OK; ++u)
+        for (int m = 0; m < 4; ++m)
+            if (cudaEventCreate(&ev[u][m]) != cudaSuccess) {
+                ev[u][m] = nullptr;
                 rc = TF_ECUDA;
                 break;
             }
-    const int has[2] = {0, 1};   // the probes are sampled inside the step: no launch of their own
-    Sources S;
-    fill_sources(h, S);
-    if (rc == TF_OK && refresh_order(h, S) != cudaSuccess) rc = TF_ECUDA;
+    auto add = [&](int kind, cudaEvent_t a, cudaEvent_t b) {
+        if (kind >= nkinds || rc != TF_OK) return;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) { rc = TF_ECUDA; return; }
+        kernel_ms[kind] += ms;
+        launches[kind] += 1;
+    };
     int64_t done = 0;
-    while (rc == TF_OK && done < nsteps) {
-        const int64_t m = (nsteps - done) < ring ? (nsteps - done) : ring;
-        for (int64_t s = 0; s < m && rc == TF_OK; ++s)
-            if (launch_one_step(h, S, ev[s]) != cudaSuccess) rc = TF_ECUDA;
+    while (rc == TF_OK && done < nunits) {
+        const int64_t m = (nunits - done) < ring ? (nunits - done) : ring;
+        bool cyc[kBatch];
+        for (int64_t u = 0; u < m && rc == TF_OK; ++u) {
+            cyc[u] = done + u < ncyc;
+            const cudaError_t e = cyc[u] ? launch_two_steps(h, S, ev[u]) : launch_one_step(h, S, ev[u]);
+            if (e != cudaSuccess) rc = TF_ECUDA;
+        }
         if (rc != TF_OK || cudaStreamSynchronize(h->stream) != cudaSuccess) { rc = TF_ECUDA; break; }
-        for (int64_t s = 0; s < m && rc == TF_OK; ++s)
-            for (int k = 0; k < nkinds; ++k) {
-                if (!has[k]) continue;
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, ev[s][k], ev[s][k + 1]) != cudaSuccess) { rc = TF_ECUDA; break; }
-                kernel_ms[k] += ms;
-                launches[k] += 1;
+        for (int64_t u = 0; u < m && rc == TF_OK; ++u) {
+            if (cyc[u]) {
+                add(2, ev[u][0], ev[u][1]);
+                add(1, ev[u][1], ev[u][2]);
+                add(1, ev[u][2], ev[u][3]);
+            } else {
+                add(1, ev[u][0], ev[u][1]);
             }
+        }
         if (rc == TF_OK && total_ms) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, ev[0][0], ev[m - 1][2]) != cudaSuccess) rc = TF_ECUDA;
+            if (cudaEventElapsedTime(&ms, ev[0][0], ev[m - 1][cyc[m - 1] ? 3 : 1]) != cudaSuccess) rc = TF_ECUDA;
             *total_ms += ms;
         }
         done += m;
     }
-    for (int64_t s = 0; s < ring; ++s)
-        for (int k = 0; k < 3; ++k)
-            if (ev[s][k]) cudaEventDestroy(ev[s][k]);
+    for (int64_t u = 0; u < ring; ++u)
+        for (int k = 0; k < 4; ++k)
+            if (ev[u][k]) cudaEventDestroy(ev[u][k]);
     free(ev);
     for (int k = 0; k < nkinds; ++k)
         if (launches[k]) kernel_ms[k] /= (double)launches[k];
@@ -733,27 +1016,29 @@ const char kCkptMagic[8] = {'T', 'F', 'C', 'K', 'P', 'T', '1', 0};
 // (nullptr where there is none)
 struct CkptPart {
     float* cur;
-    float* other;
+    float* other[2];
     size_t bytes;
 };
 
 int ckpt_parts(const tf_ctx* h, CkptPart* parts) {
     const size_t fb = sizeof(float) * (size_t)h->L.total;
+    const int x = h->cur, y = h->nxt, z = 3 - h->cur - h->nxt;
     int n = 0;
-    for (int c = 0; c < 3; ++c) parts[n++] = {h->P.E[c], h->O.E[c], fb};
-    for (int c = 0; c < 3; ++c) parts[n++] = {h->P.B[c], h->O.B[c], fb};
-    for (int c = 0; c < 3; ++c) parts[n++] = {h->P.J[c], nullptr, fb};
+    for (int c = 0; c < 3; ++c) parts[n++] = {h->fE[x][c], {h->fE[y][c], h->fE[z][c]}, fb};
+    for (int c = 0; c < 3; ++c) parts[n++] = {h->fB[x][c], {h->fB[y][c], h->fB[z][c]}, fb};
+    for (int c = 0; c < 3; ++c) parts[n++] = {h->fJ[x][c], {h->fJ[y][c], h->fJ[z][c]}, fb};
     for (int a = 0; a < 3; ++a) {
         if (h->desc.bc[a].kind != TF_BC_CPML) continue;
         for (int c = 0; c < 3; ++c)
-            if (c != a) parts[n++] = {h->P.psiB[c][a], h->O.psiB[c][a], fb};
+            if (c != a) parts[n++] = {h->fPB[x][c][a], {h->fPB[y][c][a], h->fPB[z][c][a]}, fb};
         for (int c = 0; c < 3; ++c)
-            if (c != a) parts[n++] = {h->P.psiE[c][a], nullptr, fb};
+            if (c != a) parts[n++] = {h->P.psiE[c][a], {nullptr, nullptr}, fb};
     }
     const size_t pb = sizeof(double) * TF_MAX_PROBES * TF_MAX_FREQS;
-    parts[n++] = {(float*)h->R.re, nullptr, pb};
-    parts[n++] = {(float*)h->R.im, nullptr, pb};
-    if (h->R.series) parts[n++] = {(float*)h->R.series, nullptr, sizeof(double) * (size_t)h->desc.max_probes * h->R.cap};
+    parts[n++] = {(float*)h->R.re, {nullptr, nullptr}, pb};
+    parts[n++] = {(float*)h->R.im, {nullptr, nullptr}, pb};
+    if (h->R.series)
+        parts[n++] = {(float*)h->R.series, {nullptr, nullptr}, sizeof(double) * (size_t)h->desc.max_probes * h->R.cap};
     return n;
 }
 
@@ -839,9 +1124,11 @@ tf_status tf_checkpoint_load(tf_handle h, const void* src, size_t bytes, int on_
     size_t o = kCkptHeader;
     for (int k = 0; k < n; ++k) {
         TF_CUDA(cudaMemcpyAsync(parts[k].cur, s + o, parts[k].bytes, kind, h->stream));
-        // the second buffer of a ping-pong array holds the same values, so that
-        // points the step never writes (walls) agree in both
-        if (parts[k].other) TF_CUDA(cudaMemcpyAsync(parts[k].other, s + o, parts[k].bytes, kind, h->stream));
+        // the other buffers of a rotating array hold the same values, so that
+        // points the step never writes (walls) agree in all of them
+        for (int b = 0; b < 2; ++b)
+            if (parts[k].other[b])
+                TF_CUDA(cudaMemcpyAsync(parts[k].other[b], s + o, parts[k].bytes, kind, h->stream));
         o += parts[k].bytes;
     }
     TF_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));

@@ -254,6 +254,122 @@ __global__ void k64_probe(G64 g, Prb64 R, long long level) {
     R.im[pr * TF_MAX_FREQS + k] -= s * sn * g.dt;
 }
 
+// Fused launches of the same sub-steps (one thread per point; every value a
+// thread reads from another point is one that no thread of the launch
+// writes):
+//   k64_steps_1_2   probes at level n, step 1 (B half), step 2 (Js half)
+//   k64_step_3_4    step 3 (psi_E, theta step for E), soft sources, step 4
+//                   (Js half with the new E; the Mur walls carry no Js)
+//   k64_steps_5_1_2 step 5 of step n (psi_B at the new E, B half) and, if
+//                   `next`, steps 1 and 2 of step n+1 with the probes at
+//                   level n+1 (E is not written, so both B halves use the
+//                   same curl and psi_B)
+// Walls of the Mur kind keep E^n of their planes and of the planes next to
+// them in Eold (k64_mur_walls then applies the Mur update).
+__device__ __forceinline__ void keep_mur_old(const G64& g, const int p[3], long long t) {
+    if (g.bc[2] != TF_BC_MUR) return;
+    if (p[2] == 0 || p[2] == 1 || p[2] == g.n[2] - 1 || p[2] == g.n[2])
+        for (int c = 0; c < 2; ++c) g.Eold[c][t] = g.E[c][t];
+}
+__device__ __forceinline__ void probes_at(const G64& g, const Prb64& R, long long level) {
+    if (blockIdx.x < (unsigned)R.n && threadIdx.x < TF_MAX_FREQS) {
+        const int pr = blockIdx.x, k = threadIdx.x;
+        if (k < R.nfreq[pr] && level >= R.n0[pr]) {
+            const double s = g.E[R.comp[pr]][R.q[pr]];
+            double ph = R.fdt[pr * TF_MAX_FREQS + k] * (double)level;
+            ph -= floor(ph);
+            double sn, cs;
+            sincospi(2.0 * ph, &sn, &cs);
+            R.re[pr * TF_MAX_FREQS + k] += s * cs * g.dt;
+            R.im[pr * TF_MAX_FREQS + k] -= s * sn * g.dt;
+        }
+    }
+}
+__device__ __forceinline__ double curl_E_B(const G64& g, int c, const int p[3], long long t) {
+    double r = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (a == c) continue;
+        double v = dE(g, 3 - c - a, a, p);
+        if (g.psiB[c][a]) v += g.psiB[c][a][t];
+        r += sgn(c, a) * v;
+    }
+    return r;
+}
+
+__global__ void k64_steps_1_2(G64 g, Prb64 R, long long level) {
+    probes_at(g, R, level);
+    POINT_OR_RETURN
+    keep_mur_old(g, p, t);
+    for (int c = 0; c < 3; ++c)
+        if (advanced(g, c, true, p)) g.B[c][t] -= 0.5 * g.dt * curl_E_B(g, c, p, t);
+    for (int c = 0; c < 3; ++c)
+        if (advanced(g, c, false, p) && g.kapE[c][t] > 0.0) g.J[c][t] += 0.5 * g.dt * g.kapE[c][t] * g.E[c][t];
+}
+
+__global__ void k64_step_3_4(G64 g, Src64 S) {
+    POINT_OR_RETURN
+    for (int c = 0; c < 3; ++c) {
+        if (!advanced(g, c, false, p)) continue;
+        for (int a = 0; a < 3; ++a)
+            if (a != c && g.psiE[c][a] && slab(g, a, p[a]))
+                g.psiE[c][a][t] = g.pbE[a][p[a]] * g.psiE[c][a][t] + g.pcE[a][p[a]] * dH(g, 3 - c - a, a, p);
+        double r = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            if (a == c) continue;
+            double v = dH(g, 3 - c - a, a, p);
+            if (g.psiE[c][a]) v += g.psiE[c][a][t];
+            r += sgn(c, a) * v;
+        }
+        double e = g.caE[c][t] * g.E[c][t] + g.cbE[c][t] * (r - g.J[c][t]);
+        for (int s = 0; s < S.n; ++s)
+            if (S.comp[s] == c && p[0] >= S.lo[s][0] && p[0] < S.hi[s][0] && p[1] >= S.lo[s][1] &&
+                p[1] < S.hi[s][1] && p[2] >= S.lo[s][2] && p[2] < S.hi[s][2])
+                e += S.v[s];
+        g.E[c][t] = e;
+        if (g.kapE[c][t] > 0.0) g.J[c][t] += 0.5 * g.dt * g.kapE[c][t] * e;
+    }
+}
+
+__global__ void k64_steps_5_1_2(G64 g, Prb64 R, long long level_next, int next) {
+    if (next) probes_at(g, R, level_next);
+    POINT_OR_RETURN
+    if (next) keep_mur_old(g, p, t);
+    for (int c = 0; c < 3; ++c) {
+        if (!advanced(g, c, true, p)) continue;
+        for (int a = 0; a < 3; ++a)
+            if (a != c && g.psiB[c][a] && slab(g, a, p[a]))
+                g.psiB[c][a][t] = g.pbB[a][p[a]] * g.psiB[c][a][t] + g.pcB[a][p[a]] * dE(g, 3 - c - a, a, p);
+        const double r = curl_E_B(g, c, p, t);
+        double b = g.B[c][t] - 0.5 * g.dt * r;
+        if (next) b -= 0.5 * g.dt * r;
+        g.B[c][t] = b;
+    }
+    if (next)
+        for (int c = 0; c < 3; ++c)
+            if (advanced(g, c, false, p) && g.kapE[c][t] > 0.0) g.J[c][t] += 0.5 * g.dt * g.kapE[c][t] * g.E[c][t];
+}
+
+// the Mur walls (planes 0 and n of z; blockIdx.y picks the wall)
+__global__ void k64_mur_walls(G64 g) {
+    const long long t2 = (long long)blockIdx.x * kT + threadIdx.x;
+    const long long np2 = (long long)g.N[0] * g.N[1];
+    if (t2 >= np2) return;
+    const int p[3] = {(int)(t2 % g.N[0]), (int)(t2 / g.N[0]), blockIdx.y ? g.n[2] : 0};
+    const long long t = ix(g, p[0], p[1], p[2]);
+    for (int c = 0; c < 2; ++c) {
+        bool ok = true;
+        for (int a = 0; a < 2 && ok; ++a) {
+            if (g.per[a]) continue;
+            if (a == c) ok = p[a] < g.n[a];
+            else ok = p[a] >= 1 && p[a] <= g.n[a] - 1;
+        }
+        if (!ok) continue;
+        const int ki = p[2] == 0 ? 1 : g.n[2] - 1;
+        const long long qi = ix(g, p[0], p[1], ki);
+        g.E[c][t] = g.Eold[c][qi] + g.murM * (g.E[c][qi] - g.Eold[c][t]);
+    }
+}
+
 }  // namespace
 
 struct tf64_ctx {
@@ -537,24 +653,19 @@ tf_status tf64_step(tf64_handle h, int64_t nsteps) {
         for (int a = 0; a < 3; ++a) { S.lo[s][a] = h->src[s].lo[a]; S.hi[s][a] = h->src[s].hi[a]; }
     }
     const bool mur = g.bc[2] == TF_BC_MUR;
+    const unsigned nbw = (unsigned)(((long long)g.N[0] * g.N[1] + kT - 1) / kT);
+    // two or three launches per step: steps 1 and 2 open the run, then per
+    // step the E launch (steps 3 and 4), the Mur walls, and the B launch
+    // (step 5, fused with steps 1 and 2 of the next step but the last)
+    if (nsteps > 0) k64_steps_1_2<<<nb, kT, 0, h->st>>>(g, h->R, h->level);
     for (int64_t s = 0; s < nsteps; ++s) {
-        if (h->R.n) k64_probe<<<h->R.n, TF_MAX_FREQS, 0, h->st>>>(g, h->R, h->level);
-        k64_half_B<<<nb, kT, 0, h->st>>>(g);
-        k64_half_J<<<nb, kT, 0, h->st>>>(g);
-        if (mur)
-            for (int c = 0; c < 2; ++c)
-                C64(cudaMemcpyAsync(g.Eold[c], g.E[c], sizeof(double) * (size_t)g.np, cudaMemcpyDeviceToDevice,
-                                    h->st));
-        k64_psi_E<<<nb, kT, 0, h->st>>>(g);
-        k64_E<<<nb, kT, 0, h->st>>>(g);
         const double t1 = (double)(h->level + 1) * g.dt;
         for (int q = 0; q < h->nsrc; ++q)
             S.v[q] = wave64(h->src[q].kind, h->src[q].amp, h->src[q].f, h->src[q].t0, h->src[q].tw, t1);
-        if (h->nsrc) k64_sources<<<nb, kT, 0, h->st>>>(g, S);
-        if (mur) k64_mur<<<nb, kT, 0, h->st>>>(g);
-        k64_half_J<<<nb, kT, 0, h->st>>>(g);
-        k64_psi_B<<<nb, kT, 0, h->st>>>(g);
-        k64_half_B<<<nb, kT, 0, h->st>>>(g);
+        k64_step_3_4<<<nb, kT, 0, h->st>>>(g, S);
+        if (mur) k64_mur_walls<<<dim3(nbw, 2), kT, 0, h->st>>>(g);
+        const int next = s + 1 < nsteps;
+        k64_steps_5_1_2<<<nb, kT, 0, h->st>>>(g, h->R, h->level + 1, next);
         C64(cudaGetLastError());
         h->level++;
     }

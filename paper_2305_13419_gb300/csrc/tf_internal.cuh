@@ -64,8 +64,16 @@ struct Params {
     unsigned* status;
 };
 
-// Fused step (tf_step.cu): the state ping-pongs between two buffers each
-// step; the kernel reads Params' buffers and writes these.
+// Fused step (tf_step.cu): E, B, Js and psi_B live in three buffers (the
+// current state, the next one and a scratch state for two-step passes); a
+// step reads Params' buffers and writes these.
+// Field arrays of the workspace, in the field tensor map's order: buffer b
+// holds E (index 9b + c), B (9b + 3 + c) and Js (9b + 6 + c).
+constexpr int kFieldBuffers = 3, kFieldArrays = 9 * kFieldBuffers;
+// CPML arrays of one axis, in the psi tensor map's order: the psi_B pair of
+// buffers 0 and 1, the psi_E pair, the psi_B pair of buffer 2.
+constexpr int kPsiGroup = 8;
+__host__ __device__ __forceinline__ int psib_index(int buf) { return buf == 0 ? 0 : buf == 1 ? 2 : 6; }
 constexpr int kTX = 32, kTY = 16;            // owned columns per tile (x, y)
 constexpr int kRows = 2;                     // adjacent y rows per thread: kTX x kTY / kRows threads
 constexpr int kSX = kTX, kSY = kTY;          // tile stride
@@ -77,29 +85,35 @@ constexpr int kChunk = 8;                    // z planes per work item
 // step, so the ring must hold the two planes the next item starts with
 // while that one is still in use: four stages at least.
 static_assert(kStages >= 4, "the ring must reach two planes into the next item");
-// A work-item descriptor keeps len - 1 in bits 28..30 so that it stays
-// non-negative (-1 marks the end of the work).
-static_assert(kChunk <= 8, "descriptors must stay non-negative");
+
 // per-item CPML coefficient table: kBX columns, kBY rows, kChunk + 2 planes per profile
 constexpr int kCfY = kBX, kCfZ = kBX + kBY, kCfN = 64;
 static_assert(kCfZ + kChunk + 2 <= kCfN && 4 * kCfN <= kTX * (kTY / kRows), "one table entry per thread");
 constexpr int kSub = 2;                      // planes per piece of a work item that takes the full loop
-// a work item is a descriptor: tile (bits 0-15), first plane (16-27), planes - 1 (28-31)
-constexpr int kMaxTiles = 1 << 16, kMaxPlanes = 1 << 12;
+// a work item is a 64-bit descriptor: tile (bits 0-19), first plane (20-39),
+// planes (40-47); -1 marks the end of the work
+constexpr int kMaxTiles = 1 << 20, kMaxPlanes = 1 << 20;
+__host__ __device__ __forceinline__ long long make_item(int tile, int kz0, int len) {
+    return (long long)tile | (long long)kz0 << 20 | (long long)len << 40;
+}
+__host__ __device__ __forceinline__ int item_tile(long long d) { return (int)(d & 0xfffff); }
+__host__ __device__ __forceinline__ int item_kz0(long long d) { return (int)((d >> 20) & 0xfffff); }
+__host__ __device__ __forceinline__ int item_len(long long d) { return (int)((d >> 40) & 0xff); }
 constexpr long long kSpinLimit = 1LL << 22;  // bounded mbarrier waits
 
 struct StepOut {
     float* E[3];
     float* B[3];
+    float* J[3];
     float* psiB[3][3];
     const float4* tilemat;   // per (tile, plane): {ca, cb, cj, 1/mu} of a uniform-material
                              // tile-plane, ca = NaN where the material varies
     int ntx, nty, nch;       // tiles along x, y; z chunks
     int kend;                // planes iterated: N2 (periodic z) or N2 - 1
     int ecur, bcur;          // index of the current E / B arrays in the field tensor map
-    int psi_slot[3];         // per axis: group of 6 psi arrays in the psi tensor map, -1 if no CPML
-    int psib_cur;            // 0 or 2: current psi_B pair inside a group (E pair at 4)
-    const int* order;        // work-item descriptors of a launch in the order they are handed out
+    int psi_slot[3];         // per axis: group of kPsiGroup psi arrays in the psi tensor map, -1 if no CPML
+    int psib_cur;            // 0, 2 or 6: current psi_B pair inside a group (psi_E pair at 4)
+    const long long* order;  // work-item descriptors of a launch in the order they are handed out
     int nitems;              // descriptors in `order`
     unsigned long long* ctr; // work counter (monotone across launches)
     unsigned long long base; // counter value at the start of this launch
@@ -134,6 +148,38 @@ struct Probes {
     long long cap;
     double dt;
 };
+
+// Two steps per pass (tf_step2.cu) on the interior box of a grid: every
+// point it computes lies off the walls and outside the CPML slabs and Mur
+// planes, and mu is uniform.  It reads E^n, B^{n-1/2} (TMA) and Js^{n-1/2},
+// writes E^{n+2}, B^{n+3/2}, Js^{n+3/2} to the next buffer, and the level
+// n+1 E / n+1/2 B of the points within two of the box faces (and of probe
+// points) to the third buffer, from which the single-step kernel advances
+// the rest of the grid to level n+2.
+constexpr int kTBLenMax = 16;   // planes per two-step work item
+struct Step2Out {
+    float* E[3];             // E^{n+2}, B^{n+3/2}, Jt^{n+3/2}
+    float* B[3];
+    float* J[3];
+    float* ZE[3];            // E^{n+1}, B^{n+1/2} of the ring and probe points
+    float* ZB[3];
+    const float4* tilemat;   // per (tile, plane) records of the single-step kernel
+    int ntx, nty;
+    int ecur, bcur;          // TMA array index of the E^n / B^{n-1/2} arrays
+    int lo[3], hi[3];        // the box, [lo, hi) in points (tile aligned in x, y)
+    const long long* order;  // work-item descriptors (make_item)
+    int nitems;
+    unsigned long long* ctr; // work counter (monotone across launches)
+    unsigned long long base; // counter value at the start of this launch
+    int nprobe;
+    int probe[TF_MAX_PROBES][3];
+    float amp2[TF_MAX_SOURCES];  // amp * s(t^{n+2}) (Sources::amp holds t^{n+1})
+};
+cudaError_t launch_step2(const void* tmaps2, const Params& P, const Step2Out& O, const Sources& S, int blocks,
+                         cudaStream_t st);
+int step2_blocks_per_sm();
+// TMA views for the two-step kernel's boxes (E^n 40 x 20, B^{n-1/2} 40 x 19)
+constexpr int kT2BoxX = 40, kT2BoxEY = 20, kT2BoxBY = 19;
 
 // running DFT of probe pr at level n (Secs. 4.2, 5): X_f += s^n e^{-2 pi i f_k n dt} dt in FP64,
 // for the frequency f handled by this thread, and the series sample (f = 0)
@@ -302,7 +348,7 @@ cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0
                                  float* g_lam, cudaStream_t stream);
 
 // order in which k_step hands out its work items (items needing the full plane loop first)
-cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int tail, int* order,
+cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int tail, long long* order,
                               int* count, cudaStream_t st);
 int step_blocks_per_sm();
 cudaError_t launch_field_stats(const float* f, int n0, int n1, int n2, int pitch, long long plane, double scale,

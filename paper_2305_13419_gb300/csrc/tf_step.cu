@@ -26,9 +26,9 @@
 //            shared B plane and the previous plane's B kept in registers.
 // A pair lives in 64-bit registers and moves with 64-bit shared / global
 // accesses; its arithmetic uses the packed FP32x2 add / sub / mul / fma of
-// the sm_100 family.  E, B and psi_B ping-pong between two arrays (the other
-// tiles only ever read the old ones); Js and psi_E are owned by one thread
-// and update in place.  Work items (tile, z chunk) are handed out through an
+// the sm_100 family.  E, B, Js and psi_B go from one buffer to another (the
+// other tiles only ever read the old ones); psi_E is owned by one thread and
+// updates in place.  Work items (tile, z chunk) are handed out through an
 // order that puts the slow items first, the others z chunk by z chunk and
 // the last ones in short pieces; each CTA starts with two items by position
 // and draws the rest from an atomic counter; the grid fills every SM twice.
@@ -50,11 +50,14 @@
 
 #include <type_traits>
 
+#include "tf_device.cuh"
 #include "tf_internal.cuh"
 
 namespace tf {
 
 namespace {
+
+using namespace dev;
 
 struct __align__(128) StageBuf {
     alignas(128) float e[3][kEY][kEX];    // E^n, tile + halo
@@ -83,38 +86,6 @@ struct TMaps {
     CUtensorMap e, b, pb;
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// bounded wait for phase `phase` of a barrier; false if it never completed
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase) {
-    for (long long it = 0; it < kSpinLimit; ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(phase)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, int x, int y, int z, int f,
-                                             unsigned long long* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-        "%5}], [%6];" ::"r"(smem_u32(dst)),
-        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(f), "r"(smem_u32(bar))
-        : "memory");
-}
-
 // the two components != a, ascending (the pair a CPML axis acts on)
 __host__ __device__ __forceinline__ int pair_c1(int a) { return a == 0 ? 1 : 0; }
 __host__ __device__ __forceinline__ int pair_c2(int a) { return a == 2 ? 1 : 2; }
@@ -135,21 +106,18 @@ __device__ __forceinline__ int wrap_or_out(const Params& P, int a, int v) {
 struct Tile {
     int x0, y0, kz0, kz1, ks, nq, bx, by;
 };
-__device__ __forceinline__ Tile tile_of(const Params& P, const StepOut& O, int item) {
+__device__ __forceinline__ Tile tile_of(const Params& P, const StepOut& O, long long item) {
     Tile t;
-    const int tile = item & 0xffff;   // descriptor: tile, first plane, planes - 1
+    const int tile = item_tile(item);
     t.bx = tile % O.ntx;
     t.by = tile / O.ntx;
     t.x0 = t.bx * kSX;
     t.y0 = t.by * kSY;
-    t.kz0 = (item >> 16) & 0xfff;
-    t.kz1 = t.kz0 + ((unsigned)item >> 28) + 1;
+    t.kz0 = item_kz0(item);
+    t.kz1 = t.kz0 + item_len(item);
     t.ks = (t.kz0 > 0 || P.per[2]) ? t.kz0 - 1 : t.kz0;
     t.nq = t.kz1 - t.ks + 1;   // planes pulled: ks .. kz1
     return t;
-}
-__device__ __forceinline__ int make_item(int tile, int kz0, int len) {
-    return (int)((unsigned)tile | (unsigned)kz0 << 16 | (unsigned)(len - 1) << 28);
 }
 __device__ __forceinline__ int plane_of(const Params& P, const Tile& t, int q) {
     int k = t.ks + q;
@@ -172,53 +140,6 @@ __device__ __forceinline__ int slab_axis(int bits) { return (bits & 4) ? 2 : (bi
 // position p on axis a inside its CPML slab (p may lie outside the grid)
 __device__ __forceinline__ bool slab_pos(const Params& P, int a, int p) {
     return p >= 0 && p < P.N[a] && in_slab(P, a, p);
-}
-
-// Two horizontally adjacent points travel together: a 64-bit register holds
-// the pair (low: x, high: x + 1) and the sm_100-family packed FP32 pipe
-// (add / sub / mul / fma .f32x2) updates both at once.
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 pk(float a, float b) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(__float_as_uint(a)), "r"(__float_as_uint(b)));
-    return r;
-}
-__device__ __forceinline__ float lo(f2 v) { return __uint_as_float((unsigned)(v & 0xffffffffull)); }
-__device__ __forceinline__ float hi(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
-__device__ __forceinline__ f2 add2(f2 a, f2 b) {
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-// 8-byte aligned pair in shared or global memory.  A global pair whose high
-// point lies past the grid's x end reads and writes the spare column every
-// row has there (the row pitch is at least N0 + 1); nothing reads it back.
-__device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const f2*>(p); }
-__device__ __forceinline__ void st2(float* p, f2 v) { *reinterpret_cast<f2*>(p) = v; }
-// store the points whose bit is set in m (bit 0: low, bit 1: high)
-__device__ __forceinline__ void st2m(float* p, f2 v, unsigned m) {
-    if (m == 3u)
-        st2(p, v);
-    else if (m == 1u)
-        p[0] = lo(v);
-    else if (m == 2u)
-        p[1] = hi(v);
 }
 
 struct P3 {
@@ -249,12 +170,6 @@ __device__ __forceinline__ unsigned masks_of(const Params& P, int gx0, int gy) {
 constexpr unsigned kMaskZlo = (1u << 2 | 1u << 3 | 1u << 4) * 65u;
 // the two point bits (low, high) of mask bit `b`
 __device__ __forceinline__ unsigned mbits(unsigned m, int b) { return (m >> b & 1u) | (m >> (b + 5) & 2u); }
-// per point: m bit set -> new value, else old value (a bitwise select, no branch)
-__device__ __forceinline__ f2 sel2(f2 nv, f2 ov, unsigned m2) {
-    const f2 M = (f2)(0u - (m2 & 1u)) | (f2)(0u - (m2 >> 1 & 1u)) << 32;
-    return (nv & M) | (ov & ~M);
-}
-
 // B^{n+1/2} before masking at the pair of box positions (j, i0), (j, i0 + 1)
 // of landed stages s0 (plane k) and s1 (plane k + 1): the curl update plus the
 // CPML memory of the staged axis sax (coefficients bB, cB; zero outside the
@@ -357,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     float(*bplanes)[3][kBY][kBX] = reinterpret_cast<float(*)[3][kBY][kBX]>(smem_raw + kStages * sizeof(StageBuf));
     unsigned long long* bar =
         reinterpret_cast<unsigned long long*>(smem_raw + kStages * sizeof(StageBuf) + 2 * kBPlaneBytes);
-    __shared__ int s_item[2];                   // current and next work item (-1: none)
+    __shared__ long long s_item[2];             // current and next work item (-1: none)
     __shared__ float4 s_rec[2][kChunk + 2];     // material record of each plane of the two items
     __shared__ unsigned s_flag[2][kChunk + 2];  // plane flags
     // CPML coefficients of the two items (zero outside the slabs): per profile
@@ -375,12 +290,12 @@ __global__ void __launch_bounds__(kThreads, 2)
     // (or -1); the two halves are a plane apart, so that the counter's round
     // trip does not hold up the producer's warp
     auto ticket = [&]() -> unsigned long long { return atomicAdd(O.ctr, 1ull); };
-    auto item_of = [&](unsigned long long tk) -> int {
+    auto item_of = [&](unsigned long long tk) -> long long {
         const long long d = (long long)(tk - O.base) + 2LL * gridDim.x;
-        return (d >= 0 && d < nitems) ? __ldg(O.order + d) : -1;
+        return (d >= 0 && d < nitems) ? __ldg(O.order + d) : -1LL;
     };
     // the records of an item: loaded by threads < nq - 1 ...
-    auto rec_load = [&](int item, float4& r, float& cf) {
+    auto rec_load = [&](long long item, float4& r, float& cf) {
         if (item < 0) return;
         const Tile t = tile_of(P, O, item);
         if (tid < t.nq - 1) r = __ldg(O.tilemat + (long long)(t.by * O.ntx + t.bx) * P.N[2] + plane_of(P, t, tid));
@@ -404,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
     };
     // ... and stored with the plane flags
-    auto rec_store = [&](int item, int slot, const float4& r, float cf) {
+    auto rec_store = [&](long long item, int slot, const float4& r, float cf) {
         if (item < 0) return;
         (&s_cf[slot][0][0])[tid] = cf;
         const Tile t = tile_of(P, O, item);
@@ -448,20 +363,20 @@ __global__ void __launch_bounds__(kThreads, 2)
         tma_load_box(&stg[s].e[0][0][0], &tm.e, t.x0 - 4, t.y0 - 1, k, O.ecur, &bar[s]);
         tma_load_box(&stg[s].b[0][0][0], &tm.b, t.x0 - 4, t.y0 - 1, k, O.bcur, &bar[s]);
         if (sax >= 0)
-            tma_load_box(&stg[s].pb[0][0][0], &tm.pb, t.x0 - 4, t.y0 - 1, k, 6 * O.psi_slot[sax] + O.psib_cur,
-                         &bar[s]);
+            tma_load_box(&stg[s].pb[0][0][0], &tm.pb, t.x0 - 4, t.y0 - 1, k,
+                         kPsiGroup * O.psi_slot[sax] + O.psib_cur, &bar[s]);
     };
     auto pump = [&]() {   // keep kStages planes in flight, crossing into the next item
         while (issued < consumed + kStages) {
             if (!p_have) {
-                const int item = s_item[p_ord & 1];
+                const long long item = s_item[p_ord & 1];
                 if (item < 0) return;
                 p_t = tile_of(P, O, item);
                 p_have = true;
             }
             if (p_q >= p_t.nq) {
                 if (p_ord > c_ord) return;   // the next slot still holds the current item
-                const int item = s_item[(p_ord + 1) & 1];
+                const long long item = s_item[(p_ord + 1) & 1];
                 if (item < 0) return;
                 ++p_ord;
                 p_q = 0;
@@ -477,8 +392,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         const int b = (int)blockIdx.x, g = (int)gridDim.x;
-        s_item[0] = b < nitems ? __ldg(O.order + b) : -1;
-        s_item[1] = (s_item[0] >= 0 && g + b < nitems) ? __ldg(O.order + g + b) : -1;
+        s_item[0] = b < nitems ? __ldg(O.order + b) : -1LL;
+        s_item[1] = (s_item[0] >= 0 && g + b < nitems) ? __ldg(O.order + g + b) : -1LL;
     }
     __syncthreads();
     {
@@ -499,11 +414,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     bool aborted = false;
     unsigned long long seq0 = 0;   // ring sequence number of plane 0 of the current item
     unsigned it = 0;               // planes done by this CTA (selects the shared B plane)
-    int pend = -1;                 // producer: the item after the next one
+    long long pend = -1;           // producer: the item after the next one
     unsigned long long ptk = 0;    // producer: its ticket
     bool phas = false;             // producer: a ticket was drawn for it
     while (true) {
-        const int item = s_item[cur];
+        const long long item = s_item[cur];
         if (item < 0) break;
         const Tile t = tile_of(P, O, item);
         const int x0 = t.x0, y0 = t.y0, kz0 = t.kz0, nq = t.nq;
@@ -774,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     phas = s_item[cur ^ 1] >= 0;
                     if (phas) ptk = ticket();
                 }
-                if (qq == 1 || nq == 2) pend = phas ? item_of(ptk) : -1;
+                if (qq == 1 || nq == 2) pend = phas ? item_of(ptk) : -1LL;
             }
             if (qq == 0) rec_load(s_item[cur ^ 1], rnext, cfnext);
 
@@ -922,9 +837,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                 st2(O.E[1] + q, n1);
                 st2(O.E[2] + q, n2);
                 if (sc) {
-                    st2(P.J[0] + q, jt0);
-                    st2(P.J[1] + q, jt1);
-                    st2(P.J[2] + q, jt2);
+                    st2(O.J[0] + q, jt0);
+                    st2(O.J[1] + q, jt1);
+                    st2(O.J[2] + q, jt2);
                 }
                 if (sl) {
                     const unsigned vm = v1 ? 3u : 1u;
@@ -1089,7 +1004,7 @@ cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, co
 // CTAs at work at one time then share halos in L2), the last `tail` of them
 // cut into kSub-plane pieces so that the CTAs run out of work together.
 // One CTA; writes the descriptors and their count.
-__global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Sources S, int split, int tail, int* order,
+__global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Sources S, int split, int tail, long long* order,
                                                     int* count) {
     __shared__ int s_slow[1024], s_fast[1024], s_tail[1024];
     const int n = O.ntx * O.nty * O.nch, ntiles = O.ntx * O.nty;
@@ -1163,7 +1078,7 @@ __global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Source
     if (threadIdx.x == 1023) *count = total_slow + cut + s_tail[1023];
 }
 
-cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int tail, int* order,
+cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int tail, long long* order,
                               int* count, cudaStream_t st) {
     k_item_order<<<1, 1024, 0, st>>>(P, O, S, split, tail, order, count);
     return cudaGetLastError();

@@ -26,7 +26,8 @@ TF_MAX_PROBES, TF_MAX_FREQS, TF_MAX_SOURCES = 16, 64, 16
 EXPORTS = ["tf_workspace_size", "tf_create", "tf_destroy", "tf_storage_dims", "tf_get_time", "tf_get_dt",
            "tf_set_materials", "tf_set_field", "tf_add_source", "tf_add_probe", "tf_step", "tf_sync",
            "tf_read_probe_dft", "tf_read_probe_series", "tf_read_field", "tf_fit_q", "tf_strerror",
-           "tf_step_timed", "tf_field_stats", "tf_field_stats_noalloc", "tf_checkpoint_size",
+           "tf_step_timed", "tf_set_two_step", "tf_two_step_box", "tf_field_stats", "tf_field_stats_noalloc",
+           "tf_checkpoint_size",
            "tf_checkpoint_save", "tf_checkpoint_load", "tf_adjoint_scratch_size", "tf_adjoint_run", "tf_batch_step",
            "tf64_workspace_size", "tf64_create", "tf64_destroy", "tf64_set_materials", "tf64_set_field",
            "tf64_add_source", "tf64_add_probe", "tf64_step", "tf64_sync", "tf64_read_field", "tf64_read_probe_dft",
@@ -85,6 +86,7 @@ def load(build_if_missing: bool = True):
                        ("tf_add_probe", [vp, C.c_int, ip, dp, C.c_int, C.c_int64, ip]),
                        ("tf_step", [vp, C.c_int64]), ("tf_sync", [vp]),
                        ("tf_step_timed", [vp, C.c_int64, dp, C.POINTER(C.c_int64), C.c_int, dp]),
+                       ("tf_set_two_step", [vp, C.c_int]), ("tf_two_step_box", [vp, ip, ip, ip]),
                        ("tf_read_probe_dft", [vp, C.c_int, dp, dp]),
                        ("tf_read_probe_series", [vp, C.c_int, dp, C.c_int64]),
                        ("tf_read_field", [vp, C.c_int, fp, C.c_int]),
@@ -430,14 +432,25 @@ class Grid:
 
     def step_timed(self, nsteps: int, with_total: bool = False):
         """Advance like step(); returns {kernel: (mean ms per launch, launches)}
+        for the single-step kernel ("step") and the two-step kernel ("step2")
         (and, with_total, also the whole run's event time in ms)."""
-        ms = (C.c_double * 2)()
-        cnt = (C.c_int64 * 2)()
+        ms = (C.c_double * 3)()
+        cnt = (C.c_int64 * 3)()
         tot = C.c_double()
-        _check(load().tf_step_timed(self.h, int(nsteps), ms, cnt, 2, C.byref(tot)), "tf_step_timed")
-        names = ("probe", "step")
-        kt = {names[k]: (ms[k], int(cnt[k])) for k in range(2) if cnt[k]}
+        _check(load().tf_step_timed(self.h, int(nsteps), ms, cnt, 3, C.byref(tot)), "tf_step_timed")
+        names = ("probe", "step", "step2")
+        kt = {names[k]: (ms[k], int(cnt[k])) for k in range(3) if cnt[k]}
         return (kt, tot.value) if with_total else kt
+
+    def set_two_step(self, enable: bool):
+        """Allow (default) or forbid two-step passes (temporal blocking)."""
+        _check(load().tf_set_two_step(self.h, 1 if enable else 0), "tf_set_two_step")
+
+    def two_step_box(self):
+        """((lo, hi) of the two-step box in storage points per axis, active)."""
+        lo, hi, act = (C.c_int * 3)(), (C.c_int * 3)(), C.c_int()
+        _check(load().tf_two_step_box(self.h, lo, hi, C.byref(act)), "tf_two_step_box")
+        return (tuple(lo), tuple(hi)), bool(act.value)
 
     @property
     def level(self) -> int:

@@ -293,11 +293,11 @@ def test_qfit_on_oracle_damped_oscillation():
 TABLE1 = [(float(r[0]), float(r[1]), float(r[4]) * 1e-9, float(r[5])) for r in read_table("table1_skin_depth.txt")]
 
 
-def cw_skin_depth(g, w):
+def cw_skin_depth(X, w):
     """Table 1's measure, delta = z0 / ln(E0 / E_z0): E0 the steady-state
-    amplitude (DFT over whole periods) at the interface, E_z0 the one at the
-    probe one expected depth inside."""
-    X = [abs(g.probe_dft(p, 1)[0]) for p in range(len(w.probes))]
+    amplitude (|DFT| over whole periods, X[0]) at the interface, E_z0 the one
+    at the probe one expected depth inside (X[2])."""
+    X = [abs(x) for x in X]
     z0 = (w.probes[2].p[2] - w.probes[0].p[2]) * w.d[2]
     return z0 / math.log(X[0] / X[2])
 
@@ -320,7 +320,7 @@ def test_cw_skin_depth_table1(sigma, f):
     w = W.skin_column(sigma, f, delta_th, spinup_periods=sp, window_periods=wp)
     g = stepper.Grid.from_workload(w)
     g.step(w.nsteps)
-    delta = cw_skin_depth(g, w)
+    delta = cw_skin_depth([g.probe_dft(p, 1)[0] for p in range(len(w.probes))], w)
     row = [r for r in TABLE1 if r[0] == sigma and r[1] == f][0]
     if delta_th > 2 * w.d[2]:
         assert abs(delta / row[2] - 1) < 1e-2, (delta, row)
