@@ -1,8 +1,9 @@
 // tf_fp64.cu -- FP64 GPU stepper (the precision reference of the FP32 path).
 //
 // Runs Algorithm 1 (arXiv 2305.13419, Sec. 3) as its five sub-steps in FP64,
-// SI units, on the integer-level state, one kernel per sub-step and one
-// thread per storage point:
+// SI units, on the integer-level state, in their order, one thread per
+// storage point (two launches per step, three with Mur walls: see the
+// fused launches below):
 //   sample probes (E^n)
 //   1  B  -= dt/2 curl E            (CPML memory psi_B as it stands)
 //   2  Js += dt/2 kappa E           (superconducting edges)
@@ -14,8 +15,9 @@
 // with edge values from cell values by the same rule as the FP32 path (eps:
 // mean of the 4 cells; sigma, kappa: mean over the conducting /
 // superconducting cells or plain mean; mu on a face: mean of its 2 cells) and
-// the same Roden-Gedney CPML.  Bandwidth-bound by design: it exists to
-// measure how far the FP32 fused step drifts from FP64 arithmetic.
+// the same Roden-Gedney CPML.  It exists to measure how far the FP32 fused
+// step drifts from FP64 arithmetic; the FP64 pipe (1/64 of the FP32 rate on
+// this part) bounds it.
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -142,39 +144,6 @@ __device__ __forceinline__ double dH(const G64& g, int h, int a, const int p[3])
     return (__dmul_rn(g.B[h][i0], g.imuF[h][i0]) - __dmul_rn(g.B[h][i1], g.imuF[h][i1])) * g.id[a];
 }
 
-// steps 1 and 5: B -= dt/2 curl E (with psi_B)
-__global__ void k64_half_B(G64 g) {
-    POINT_OR_RETURN
-    for (int c = 0; c < 3; ++c) {
-        if (!advanced(g, c, true, p)) continue;
-        double r = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            if (a == c) continue;
-            double v = dE(g, 3 - c - a, a, p);
-            if (g.psiB[c][a]) v += g.psiB[c][a][t];
-            r += sgn(c, a) * v;
-        }
-        g.B[c][t] -= 0.5 * g.dt * r;
-    }
-}
-
-// steps 2 and 4
-__global__ void k64_half_J(G64 g) {
-    POINT_OR_RETURN
-    for (int c = 0; c < 3; ++c)
-        if (advanced(g, c, false, p) && g.kapE[c][t] > 0.0) g.J[c][t] += 0.5 * g.dt * g.kapE[c][t] * g.E[c][t];
-}
-
-__global__ void k64_psi_E(G64 g) {
-    POINT_OR_RETURN
-    for (int c = 0; c < 3; ++c) {
-        if (!advanced(g, c, false, p)) continue;
-        for (int a = 0; a < 3; ++a)
-            if (a != c && g.psiE[c][a] && slab(g, a, p[a]))
-                g.psiE[c][a][t] = g.pbE[a][p[a]] * g.psiE[c][a][t] + g.pcE[a][p[a]] * dH(g, 3 - c - a, a, p);
-    }
-}
-
 __global__ void k64_psi_B(G64 g) {
     POINT_OR_RETURN
     for (int c = 0; c < 3; ++c) {
@@ -185,55 +154,10 @@ __global__ void k64_psi_B(G64 g) {
     }
 }
 
-// step 3 (theta scheme), in place: curl H reads only B, so every thread owns
-// the E it writes
-__global__ void k64_E(G64 g) {
-    POINT_OR_RETURN
-    for (int c = 0; c < 3; ++c) {
-        if (!advanced(g, c, false, p)) continue;
-        double r = 0.0;
-        for (int a = 0; a < 3; ++a) {
-            if (a == c) continue;
-            double v = dH(g, 3 - c - a, a, p);
-            if (g.psiE[c][a]) v += g.psiE[c][a][t];
-            r += sgn(c, a) * v;
-        }
-        g.E[c][t] = g.caE[c][t] * g.E[c][t] + g.cbE[c][t] * (r - g.J[c][t]);
-    }
-}
-
 struct Src64 {
     int n, comp[TF_MAX_SOURCES], lo[TF_MAX_SOURCES][3], hi[TF_MAX_SOURCES][3];
     double v[TF_MAX_SOURCES];
 };
-
-__global__ void k64_sources(G64 g, Src64 S) {
-    POINT_OR_RETURN
-    for (int s = 0; s < S.n; ++s) {
-        const int c = S.comp[s];
-        if (p[0] >= S.lo[s][0] && p[0] < S.hi[s][0] && p[1] >= S.lo[s][1] && p[1] < S.hi[s][1] &&
-            p[2] >= S.lo[s][2] && p[2] < S.hi[s][2] && advanced(g, c, false, p))
-            g.E[c][t] += S.v[s];
-    }
-}
-
-// first-order Mur on the z walls: E_w' = E_i(old) + M (E_i' - E_w(old))
-__global__ void k64_mur(G64 g) {
-    POINT_OR_RETURN
-    if (p[2] != 0 && p[2] != g.n[2]) return;
-    for (int c = 0; c < 2; ++c) {
-        bool ok = true;
-        for (int a = 0; a < 2 && ok; ++a) {
-            if (g.per[a]) continue;
-            if (a == c) ok = p[a] < g.n[a];
-            else ok = p[a] >= 1 && p[a] <= g.n[a] - 1;
-        }
-        if (!ok) continue;
-        const int ki = p[2] == 0 ? 1 : g.n[2] - 1;
-        const long long qi = ix(g, p[0], p[1], ki);
-        g.E[c][t] = g.Eold[c][qi] + g.murM * (g.E[c][qi] - g.Eold[c][t]);
-    }
-}
 
 struct Prb64 {
     int n, comp[TF_MAX_PROBES], nfreq[TF_MAX_PROBES];
@@ -241,18 +165,6 @@ struct Prb64 {
     const double* fdt;   // [probe][TF_MAX_FREQS]
     double *re, *im;
 };
-
-__global__ void k64_probe(G64 g, Prb64 R, long long level) {
-    const int pr = blockIdx.x, k = threadIdx.x;
-    if (pr >= R.n || k >= R.nfreq[pr] || level < R.n0[pr]) return;
-    const double s = g.E[R.comp[pr]][R.q[pr]];
-    double ph = R.fdt[pr * TF_MAX_FREQS + k] * (double)level;
-    ph -= floor(ph);
-    double sn, cs;
-    sincospi(2.0 * ph, &sn, &cs);
-    R.re[pr * TF_MAX_FREQS + k] += s * cs * g.dt;
-    R.im[pr * TF_MAX_FREQS + k] -= s * sn * g.dt;
-}
 
 // Fused launches of the same sub-steps (one thread per point; every value a
 // thread reads from another point is one that no thread of the launch
