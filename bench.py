@@ -80,9 +80,15 @@ def replica_seed(rank: int) -> int:
     return W.BASE_SEED + 5 + 1000 * rank
 
 
+WORKLOAD = "large"
+
+
 def headline_workload(rank: int = 0):
-    """The 1024 x 512 x 256 CPW (the largest single-GPU configuration)."""
+    """The 1024 x 512 x 256 CPW (the largest single-GPU configuration); with
+    --workload cpw the 512 x 256 x 128 CPW instead (small profiling runs)."""
     from paper_2305_13419_gb300 import workloads as W
+    if WORKLOAD == "cpw":
+        return W.cpw(seed=W.BASE_SEED + 2 + 1000 * rank)
     return W.cpw_large(seed=replica_seed(rank))
 
 
@@ -146,20 +152,29 @@ class ClockSampler:
 TILE_SX, TILE_SY = 32, 16   # owned columns per tile of the fused step kernel
 
 
-def algorithmic_bytes(w, N):
-    """Algorithmic HBM bytes per launch of the fused step kernel, each array
-    element moved once (FP32):
+def algorithmic_bytes(w, N, box=None):
+    """Algorithmic HBM bytes of the fused step kernels, each array element
+    moved once per launch (FP32):
       48 B per storage point   E read + write, B read + write;
       12 B per point of a tile-plane whose cells are not all alike
                                (eps, sigma, kappa maps; uniform tile-planes use
                                one precomputed record instead);
        8 B per superconducting edge (Js read + write);
       32 B per CPML slab point and slab axis (two psi_B read old + write new,
-                               two psi_E read + write)."""
+                               two psi_E read + write).
+    `box` ((lo, hi) in storage points): the two-step kernel's interior box;
+    then "box" holds the bytes of one two-step launch (the box's points, two
+    steps per pass) and "rest" those of one single-step launch over the
+    other points."""
     # points the kernel owns: cells of a walled axis, all points of a periodic
     # one, planes below the top wall along z
     own = [N[a] if w.bc[a] == "periodic" else w.n[a] for a in range(3)]
+    inbox = np.zeros((own[2], own[1], own[0]), bool)
+    if box is not None:
+        (lo, hi) = box
+        inbox[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = True
     pts = own[0] * own[1] * own[2]
+    pts_box = int(inbox.sum())
     psi = 0
     for a in range(3):
         if w.bc[a] != "cpml":
@@ -168,19 +183,21 @@ def algorithmic_bytes(w, N):
         psi += (2 * L) * (pts // own[a])
     # superconducting edges: an E_c edge is SC if any of its four cells is
     sc = w.lambda_L > 0
-    sc_edges = 0
+    sc_edges = sc_box = 0
     for c in range(3):
         m = sc.copy()
         for ax in [2 - b for b in range(3) if b != c]:
             m = m | np.roll(m, 1, axis=ax)
         sc_edges += int(m.sum())
-    # points in non-uniform tile-planes (cells x0-1..x0+31, y0-1..y0+7, k-1..k)
+        mm = m[:own[2], :own[1], :own[0]]
+        sc_box += int((mm & inbox[:mm.shape[0], :mm.shape[1], :mm.shape[2]]).sum())
+    # points in non-uniform tile-planes (cells x0-1..x0+31, y0-1..y0+15, k-1..k)
     per = [w.bc[a] == "periodic" for a in range(3)]
     key = np.stack([w.eps_r, w.sigma, w.lambda_L, w.mu_r], axis=-1)
     kidx = np.arange(own[2])
     kz = [np.clip(kidx - 1, 0, w.n[2] - 1) if not per[2] else (kidx - 1) % w.n[2],
           np.clip(kidx, 0, w.n[2] - 1)]
-    nonuni = 0
+    nonuni = nonuni_box = 0
     for by in range((N[1] + TILE_SY - 1) // TILE_SY):
         ys = np.arange(by * TILE_SY - 1, by * TILE_SY + TILE_SY)   # y0-1 .. y0+15
         ys = ys % w.n[1] if per[1] else np.clip(ys, 0, w.n[1] - 1)
@@ -195,9 +212,17 @@ def algorithmic_bytes(w, N):
             refk = ref[:, 0, 0]
             uni = same_plane[kz[0]] & same_plane[kz[1]] & np.all(refk[kz[0]] == refk[kz[1]], axis=-1)
             nonuni += int((~uni).sum()) * own_x * own_y
+            if box is not None and box[0][0] <= bx * TILE_SX < box[1][0] and box[0][1] <= by * TILE_SY < box[1][1]:
+                nonuni_box += int((~uni[box[0][2]:box[1][2]]).sum()) * own_x * own_y
     step = 48 * pts + 12 * nonuni + 8 * sc_edges + 32 * psi
-    return {"step": step, "points": pts, "sc_edges": sc_edges, "psi_points": psi, "nonuniform_points": nonuni,
-            "dense_equivalent": 84 * pts + 32 * psi}
+    out = {"step": step, "points": pts, "sc_edges": sc_edges, "psi_points": psi, "nonuniform_points": nonuni,
+           "dense_equivalent": 84 * pts + 32 * psi}
+    if box is not None:
+        out["box"] = 48 * pts_box + 12 * nonuni_box + 8 * sc_box
+        out["box_points"] = pts_box
+        out["rest"] = step - out["box"]
+        out["rest_points"] = pts - pts_box
+    return out
 
 
 def source_hash():
@@ -292,26 +317,60 @@ def run_reference(args, ws, rank):
 
 
 def config_block(state_bytes=None):
-    c = {"workload": "cpw-1024x512x256: CPW resonator, CPML 16, lambda_L = 4 cells, sigma_n ~ U[0,1e6] S/m, "
-                     "theta = 1, Courant 0.95, +/- Gaussian-sine port source, 2 probes x 64-frequency DFT",
-         "cells": 1024 * 512 * 256, "parallelism": "replicas (independent resonator per GPU)"}
+    if WORKLOAD == "cpw":
+        c = {"workload": "cpw-512x256x128: CPW resonator, CPML 12, lambda_L = 3 cells, sigma_n ~ U[0,1e6] S/m, "
+                         "theta = 1, Courant 0.95, +/- Gaussian-sine port source, 2 probes x 64-frequency DFT",
+             "cells": 512 * 256 * 128, "parallelism": "replicas (independent resonator per GPU)"}
+    else:
+        c = {"workload": "cpw-1024x512x256: CPW resonator, CPML 16, lambda_L = 4 cells, sigma_n ~ U[0,1e6] S/m, "
+                         "theta = 1, Courant 0.95, +/- Gaussian-sine port source, 2 probes x 64-frequency DFT",
+             "cells": 1024 * 512 * 256, "parallelism": "replicas (independent resonator per GPU)"}
     if state_bytes:
         c["l2"] = f"inputs larger than L2: {state_bytes / 2**20:.0f} MiB of fields and maps per step > 129 MiB"
     return c
 
 
-def roofline_of(w, N, kt, kernel="k_step"):
-    """Roofline of the fused step kernel: its algorithmic bytes per launch
-    over its mean event-timed launch duration, against the measured HBM peak."""
-    ab = algorithmic_bytes(w, N)
+def roofline_of(w, g, kt):
+    """Roofline of the step kernels from their algorithmic bytes per launch
+    over their mean event-timed launch durations, against the measured HBM
+    peak.  With two-step passes the two-step kernel (the interior box, two
+    steps per launch) and the single-step kernel (the rest of the grid, one
+    step per launch) are listed apart; the dominant one (larger share of the
+    run's kernel time) heads the object."""
     peak, peak_kind = hbm_peak()
-    step_s = kt["step"][0] * 1e-3
-    achieved = ab["step"] / step_s / 1e9
-    return ab, {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(kernel, w.name), "algorithmic_bytes": ab["step"],
+    (lo, hi), active = g.two_step_box()
+    two = "step2" in kt
+    ab = algorithmic_bytes(w, g.N, (lo, hi) if two else None)
+    kernels = {}
+    if two:
+        kernels["k_step2"] = {"algorithmic_bytes": ab["box"], "points": ab["box_points"], "steps_per_launch": 2,
+                              "ms": kt["step2"][0], "launches": kt["step2"][1]}
+        kernels["k_step"] = {"algorithmic_bytes": ab["rest"], "points": ab["rest_points"], "steps_per_launch": 1,
+                             "ms": kt["step"][0], "launches": kt["step"][1]}
+    else:
+        kernels["k_step"] = {"algorithmic_bytes": ab["step"], "points": ab["points"], "steps_per_launch": 1,
+                             "ms": kt["step"][0], "launches": kt["step"][1]}
+    for k, v in kernels.items():
+        v["achieved_GBps"] = v["algorithmic_bytes"] / (v["ms"] * 1e-3) / 1e9
+        v["frac"] = v["achieved_GBps"] / peak
+        v["share"] = v["ms"] * v["launches"]
+        v["traffic"] = ncu_traffic(k, w.name)
+    tot = sum(v["share"] for v in kernels.values())
+    for v in kernels.values():
+        v["share"] /= tot
+    dom = max(kernels, key=lambda k: kernels[k]["share"])
+    d = kernels[dom]
+    # effective bandwidth: the dense one-pass byte count of every step the run
+    # made (a two-step pass launches the single-step kernel twice, so the steps
+    # equal the single-step kernel's launches), over the kernels' time
+    nsteps = max(1, kernels["k_step"]["launches"])
+    ms_per_step = sum(v["ms"] * v["launches"] for v in kernels.values()) / nsteps
+    return ab, {"bound": "hbm", "kernel": dom, "achieved": d["achieved_GBps"], "peak": peak, "unit": "GB/s",
+                "frac": d["frac"], "traffic": d["traffic"], "algorithmic_bytes": d["algorithmic_bytes"],
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-                "dense_equivalent_GBps": ab["dense_equivalent"] / step_s / 1e9,
-                "effective_frac_dense_equivalent": ab["dense_equivalent"] / step_s / 1e9 / peak,
+                "kernels": kernels,
+                "dense_equivalent_GBps": ab["dense_equivalent"] / (ms_per_step * 1e-3) / 1e9,
+                "effective_frac_dense_equivalent": ab["dense_equivalent"] / (ms_per_step * 1e-3) / 1e9 / peak,
                 "kernel_ms": {k: v[0] for k, v in kt.items()}}
 
 
@@ -326,7 +385,12 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local)
     w = headline_workload(rank)
     g = tf.Grid.from_workload(w)
-    g.set_two_step(args.two_step != "off")
+    tuning = None
+    if args.two_step == "off":
+        g.set_two_step(0)
+    elif not args.no_autotune:   # the temporal-block depth and item length, from measured runs
+        from paper_2305_13419_gb300 import autotune
+        tuning = autotune.tune_grid(g, steps=args.autotune_steps)
     N = g.N
 
     # device-timed throughput: inputs resident in HBM, K steps between
@@ -344,9 +408,9 @@ def run_ours(args, ws, rank, local):
     g.sync()
     ms_max = max_over_ranks(dist, ms, dev)
     value = aggregate(w.ncells, args.steps, ms_max, ws)
-    ab, roof = roofline_of(w, N, kt)
+    ab, roof = roofline_of(w, g, kt)
     state_bytes = (9 + 3) * 4 * ab["points"]
-    launches_per_step = len(kt)
+    launches = sum(v[1] for v in kt.values())
     g.close()
     del g
     torch.cuda.empty_cache()
@@ -365,20 +429,26 @@ def run_ours(args, ws, rank, local):
     del w
     if rank == 0 and not args.no_configs:
         two = args.two_step != "off"
-        extra = {"cpw-512x256x128": run_config(W.cpw(), args.cpw_steps, 20, two),
-                 "slab-4x4x2048": run_config(W.slab(), 4000, 50, two)}
+        at = 0 if args.no_autotune else args.autotune_steps
+        extra = {"cpw-512x256x128": run_config(W.cpw(), args.cpw_steps, 20, two, at),
+                 "slab-4x4x2048": run_config(W.slab(), 4000, 50, two, 0)}
     plain_small = extra["cpw-512x256x128"]["gcell_updates_per_s"] if extra else None
     if rank == 0 and not args.no_adjoint:
         adj = run_adjoint(args)
     if rank == 0 and not args.no_batch:
-        batch = run_batch(args, plain_small or value / ws)
+        weights = None
+        if not args.no_autotune:   # CTA shares of the batch from each grid's measured step time
+            from paper_2305_13419_gb300 import autotune
+            from paper_2305_13419_gb300 import workloads as W
+            weights = autotune.batch_weights(W.cpw_batch(), steps=10)
+        batch = run_batch(args, plain_small or value / ws, weights)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_block(state_bytes), "roofline": roof, "cpu_baseline": base, "e2e": e2e,
-                "gpu_launches": launches_per_step * args.steps, "clocks": clk.summary(), "adjoint": adj,
+                "gpu_launches": launches, "clocks": clk.summary(), "autotune": tuning, "adjoint": adj,
                 "batched": batch, "other_configs": extra}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -418,10 +488,12 @@ def run_adjoint(args):
             "includes": "forward with checkpoints, per-segment recompute, adjoint steps, gradient reduction"}
 
 
-def run_batch(args, plain_gcells):
-    """The batched workload: 64 CPW variants with axes from {96, 128, 160},
-    stepped together by tf_batch_step with the grids spread over 8 streams,
-    and, for comparison, the same grids on one stream."""
+def run_batch(args, plain_gcells, weights=None):
+    """The batched workload: 64 CPW variants with axes from {96, 128, 160}.
+    Headline: tf_batch_run, one launch per step over all 64 grids (CTAs split
+    among the grids by `weights`, else by cells with CPML cells counted 2.5
+    times), 64 steps per CUDA graph, timed with CUDA events on its stream;
+    beside it tf_batch_step (per-grid launches spread over 8 streams)."""
     import time
     import torch
     from paper_2305_13419_gb300 import twofluid as tf
@@ -429,26 +501,45 @@ def run_batch(args, plain_gcells):
     ws = W.cpw_batch()
     cells = sum(w.ncells for w in ws)
     out = {"grids": len(ws), "cells": cells, "steps": args.batch_steps, "sizes": [96, 128, 160]}
-    for nstreams in (8, 1):
-        streams = [torch.cuda.Stream() for _ in range(nstreams)]
-        grids = [tf.Grid.from_workload(w, stream=streams[i % nstreams]) for i, w in enumerate(ws)]
-        tf.batch_step(grids, 10)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        tf.batch_step(grids, args.batch_steps)
-        torch.cuda.synchronize()
-        ms = (time.perf_counter() - t0) * 1e3
-        for gg in grids:
-            gg.sync()
-            gg.close()
-        del grids
-        torch.cuda.empty_cache()
-        key = "streams8" if nstreams == 8 else "one_stream"
-        out[key] = {"ms_per_step": ms / args.batch_steps,
-                    "gcell_updates_per_s": cells * args.batch_steps / (ms * 1e-3) / 1e9}
-    out["gcell_updates_per_s"] = out["streams8"]["gcell_updates_per_s"]
+    grids = [tf.Grid.from_workload(w) for w in ws]
+    tf.batch_run(grids, 10, weights)
+    torch.cuda.synchronize()
+    st = grids[0].stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    tf.batch_run(grids, args.batch_steps, weights)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    for gg in grids:
+        gg.sync()
+        gg.close()
+    del grids
+    torch.cuda.empty_cache()
+    out["one_launch"] = {"ms_per_step": ms / args.batch_steps,
+                         "gcell_updates_per_s": cells * args.batch_steps / (ms * 1e-3) / 1e9,
+                         "weights": "autotuned" if weights is not None else "cells, CPML cells x 2.5",
+                         "timing": "CUDA events on the batch's stream around tf_batch_run (includes its set-up "
+                                   "uploads and graph capture)"}
+    streams = [torch.cuda.Stream() for _ in range(8)]
+    grids = [tf.Grid.from_workload(w, stream=streams[i % 8]) for i, w in enumerate(ws)]
+    tf.batch_step(grids, 10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tf.batch_step(grids, args.batch_steps)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    for gg in grids:
+        gg.sync()
+        gg.close()
+    del grids
+    torch.cuda.empty_cache()
+    out["streams8"] = {"ms_per_step": ms / args.batch_steps,
+                       "gcell_updates_per_s": cells * args.batch_steps / (ms * 1e-3) / 1e9,
+                       "timing": "host wall clock around the enqueue of all steps, device synchronised on both sides"}
+    out["gcell_updates_per_s"] = out["one_launch"]["gcell_updates_per_s"]
     out["vs_plain_step"] = out["gcell_updates_per_s"] / plain_gcells
-    out["timing"] = "host wall clock around the enqueue of all steps, device synchronised on both sides"
+    out["plain_step"] = {"workload": "cpw-512x256x128", "gcell_updates_per_s": plain_gcells}
     return out
 
 
@@ -479,7 +570,7 @@ def run_batch_singles(args):
     return 0
 
 
-def run_config(w, steps, warmup=5, two_step=True):
+def run_config(w, steps, warmup=5, two_step=True, autotune_steps=0):
     """GPU throughput of the plain step on one workload: the whole run and
     the step kernel's own launches timed with CUDA events on the handle's
     stream over the same launches; the kernel's algorithmic bytes over its
@@ -487,18 +578,23 @@ def run_config(w, steps, warmup=5, two_step=True):
     import torch
     from paper_2305_13419_gb300 import twofluid as tf
     g = tf.Grid.from_workload(w)
-    g.set_two_step(two_step)
+    tuning = None
+    if not two_step:
+        g.set_two_step(0)
+    elif autotune_steps:
+        from paper_2305_13419_gb300 import autotune
+        tuning = autotune.tune_grid(g, steps=autotune_steps)
     g.step(warmup)
     g.sync()
     torch.cuda.synchronize()
     kt, ms = g.step_timed(steps, with_total=True)
     g.sync()
-    _, roof = roofline_of(w, g.N, kt)
+    _, roof = roofline_of(w, g, kt)
     g.close()
     del g
     torch.cuda.empty_cache()
     return {"workload": w.name, "cells": w.ncells, "steps": steps, "ms_per_step": ms / steps,
-            "gcell_updates_per_s": w.ncells * steps / (ms * 1e-3) / 1e9, "roofline": roof}
+            "gcell_updates_per_s": w.ncells * steps / (ms * 1e-3) / 1e9, "roofline": roof, "autotune": tuning}
 
 
 def run_all_configs(args):
@@ -635,6 +731,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--cpw-steps", type=int, default=2000, help="steps of the 512 x 256 x 128 CPW line")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default settings")
+    ap.add_argument("--autotune-steps", type=int, default=20, help="steps timed per autotuner candidate")
+    ap.add_argument("--workload", choices=("large", "cpw"), default="large",
+                    help="the timed workload: the 1024 x 512 x 256 CPW (default) or the 512 x 256 x 128 one")
     ap.add_argument("--two-step", choices=("auto", "off"), default="auto",
                     help="two steps per pass on the interior box where the grid has one (auto) or single steps only")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
@@ -655,6 +755,8 @@ def main(argv=None):
     ap.add_argument("--adjoint-steps", type=int, default=8000)
     ap.add_argument("--adjoint-segment", type=int, default=256, help="steps between the adjoint's checkpoints")
     args = ap.parse_args(argv)
+    global WORKLOAD
+    WORKLOAD = args.workload
     ws, rank, local = dist_env()
     if args.warmup < 3:
         args.warmup = 3

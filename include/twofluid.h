@@ -189,13 +189,14 @@ tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t*
  * same bits as single steps.  It is used when the box is not empty, mu is
  * uniform (tf_set_materials) and it is enabled; an odd step count ends with a
  * single step.
- *   tf_set_two_step  enable (1, the default) or disable (0) it for this
- *                    handle (TF_EINVAL for other values); a tuning switch,
- *                    results do not change.
+ *   tf_set_two_step  planes = 0 disables it for this handle; 4 .. 16 enables
+ *                    it with work items of that many planes (16 by default);
+ *                    other values TF_EINVAL.  A tuning switch (the project's
+ *                    autotuner sets it per grid): results do not change.
  *   tf_two_step_box  the box in storage points, [lo, hi) per axis (all zero
  *                    when the geometry has none), and in *active (may be
  *                    NULL) whether tf_step uses it. */
-tf_status tf_set_two_step(tf_handle h, int enable);
+tf_status tf_set_two_step(tf_handle h, int planes);
 tf_status tf_two_step_box(tf_handle h, int lo[3], int hi[3], int* active);
 
 /* Advance n independent grids by nsteps steps each (the batched workload:
@@ -205,6 +206,26 @@ tf_status tf_two_step_box(tf_handle h, int lo[3], int hi[3], int* active);
  * beside the next grid's first ones).  Handles must be distinct; the call
  * returns after enqueueing (use tf_sync per handle). */
 tf_status tf_batch_step(const tf_handle* hs, int n, int64_t nsteps);
+
+/* One launch per step over every grid of a batch (many resonator variants
+ * of uneven sizes): the single-step kernel's CTAs are split among the grids
+ * in proportion to their work (`weights`, e.g. an autotuner's measured times
+ * per step, or NULL for cells with CPML slab cells counted 2.5 times), each
+ * CTA takes work items of its grid only, and 64 steps at a time are captured
+ * in a CUDA graph and replayed (the step number lives on the device and a
+ * one-thread launch advances it after each step).  Every grid ends with the
+ * same bits as tf_step (single steps) would give it.
+ *   hs, n      handles (distinct, n <= the CTA slots of the device, else
+ *              TF_ENOTSUP); the run is issued on hs[0]'s stream after every
+ *              handle's stream has been synchronised, and synchronises it;
+ *   weights    n positive numbers or NULL;
+ *   scratch    caller-owned device memory (256-byte aligned) of at least
+ *              tf_batch_scratch_size bytes: the per-grid arguments and the
+ *              source amplitudes of every step (TF_ENOMEM if smaller).
+ * Creating the CUDA graph may make the CUDA runtime allocate. */
+tf_status tf_batch_scratch_size(const tf_handle* hs, int n, int64_t nsteps, size_t* bytes);
+tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, const double* weights, void* scratch,
+                       size_t bytes);
 
 /* Wait for the stream and return the latched device status
  * (TF_ENONFINITE if the watchdog saw a non-finite E). */

@@ -145,6 +145,7 @@ struct tf_ctx {
     unsigned long long* ctr_t;
     unsigned long long base_t;
     int two_step_on;    // two-step passes allowed (tf_set_two_step; on by default)
+    int tb_len;         // planes per two-step work item
     int ppos[TF_MAX_PROBES][3];   // probe points (storage coordinates)
     Probes R;
     cudaStream_t stream;
@@ -418,6 +419,7 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
     h->ctr_t = (unsigned long long*)(base + L.off_misc + 160);
     h->base_t = 0;
     h->two_step_on = 1;
+    h->tb_len = kTBLenMax;
     P.status = h->status;
     {
         int dev = 0, sms = 1;
@@ -747,8 +749,8 @@ cudaError_t build_two_step_lists(tf_ctx* h, const Sources& S) {
         for (int k = kz0; k < kz0 + len; k += kSub)
             sl[ns++] = make_item(tile, k, (kz0 + len - k) < kSub ? kz0 + len - k : kSub);
     }
-    for (int kz = h->tz0; kz < h->tz1; kz += kTBLenMax) {
-        const int len = h->tz1 - kz < kTBLenMax ? h->tz1 - kz : kTBLenMax;
+    for (int kz = h->tz0; kz < h->tz1; kz += h->tb_len) {
+        const int len = h->tz1 - kz < h->tb_len ? h->tz1 - kz : h->tb_len;
         for (int ty = h->ty0; ty < h->ty1; ++ty)
             for (int tx = h->tx0; tx < h->tx1; ++tx)
                 tl[nt++] = make_item(ty * L.ntx + tx, kz, len);
@@ -826,9 +828,13 @@ tf_status tf_step(tf_handle h, int64_t nsteps) {
     return TF_OK;
 }
 
-tf_status tf_set_two_step(tf_handle h, int enable) {
-    if (!h || (enable != 0 && enable != 1)) return TF_EINVAL;
-    h->two_step_on = enable;
+tf_status tf_set_two_step(tf_handle h, int planes) {
+    if (!h || (planes != 0 && (planes < 4 || planes > kTBLenMax))) return TF_EINVAL;
+    h->two_step_on = planes != 0;
+    if (planes != 0 && planes != h->tb_len) {
+        h->tb_len = planes;
+        h->order_dirty = 1;   // the box's work list is cut again
+    }
     return TF_OK;
 }
 
@@ -878,6 +884,202 @@ tf_status tf_batch_step(const tf_handle* hs, int n, int64_t nsteps) {
             }
         }
     return TF_OK;
+}
+
+// ---------------------------------------------------------------- batches
+namespace {
+
+constexpr int kBatchGraphSteps = 64;   // steps per captured graph
+
+struct BatchLayout {
+    size_t off_step, off_grids, off_amp, bytes;
+};
+
+BatchLayout batch_layout(const tf_handle* hs, int n, int64_t nsteps) {
+    BatchLayout B{};
+    size_t o = 0;
+    B.off_step = o;  o += kAlign;
+    B.off_grids = o; o += align_up(sizeof(BatchGrid) * (size_t)n);
+    B.off_amp = o;
+    for (int i = 0; i < n; ++i) o += align_up(sizeof(float) * (size_t)nsteps * (size_t)(hs[i]->nsrc > 0 ? hs[i]->nsrc : 1));
+    B.bytes = o;
+    return B;
+}
+
+tf_status batch_check(const tf_handle* hs, int n, int64_t nsteps) {
+    if (!hs || n < 1 || nsteps < 0) return TF_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) return TF_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) return TF_EINVAL;   // a handle twice would race with itself
+    }
+    return TF_OK;
+}
+
+}  // namespace
+
+tf_status tf_batch_scratch_size(const tf_handle* hs, int n, int64_t nsteps, size_t* bytes) {
+    tf_status rc = batch_check(hs, n, nsteps);
+    if (rc != TF_OK) return rc;
+    if (!bytes) return TF_EINVAL;
+    *bytes = batch_layout(hs, n, nsteps).bytes;
+    return TF_OK;
+}
+
+tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, const double* weights, void* scratch,
+                       size_t bytes) {
+    tf_status rc = batch_check(hs, n, nsteps);
+    if (rc != TF_OK) return rc;
+    if (!scratch || ((uintptr_t)scratch) % kAlign) return TF_EINVAL;
+    const BatchLayout BL = batch_layout(hs, n, nsteps);
+    if (bytes < BL.bytes) return TF_ENOMEM;
+    if (nsteps == 0) return TF_OK;
+    const int slots = hs[0]->slots;
+    if (n > slots) return TF_ENOTSUP;   // every grid needs a CTA of its own
+    if (weights)
+        for (int i = 0; i < n; ++i)
+            if (!(weights[i] > 0) || !isfinite(weights[i])) return TF_EINVAL;
+    // the grids' earlier work is done before the batch reads their state
+    for (int i = 0; i < n; ++i) TF_CUDA(cudaStreamSynchronize(hs[i]->stream));
+    cudaStream_t st = hs[0]->stream;
+    // CTAs per grid in proportion to its work: the caller's weights (an
+    // autotuner's measured times per step), else cells with CPML slab cells counted 2.5 times
+    double* w = (double*)malloc(sizeof(double) * (size_t)n);
+    int* cnt = (int*)malloc(sizeof(int) * (size_t)n);
+    BatchGrid* G = (BatchGrid*)calloc((size_t)n, sizeof(BatchGrid));
+    char* amp_host = (char*)malloc(BL.bytes - BL.off_amp);
+    if (!w || !cnt || !G || !amp_host) {
+        free(w); free(cnt); free(G); free(amp_host);
+        return TF_ENOMEM;
+    }
+    double W = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const tf_ctx* h = hs[i];
+        if (weights) {
+            w[i] = weights[i];
+        } else {
+            double inner = 1.0;
+            for (int a = 0; a < 3; ++a) inner *= 1.0 - 2.0 * h->P.L[a] / (double)h->P.n[a];
+            w[i] = (double)h->L.ncell * (1.0 + 1.5 * (1.0 - inner));
+        }
+        W += w[i];
+    }
+    int used = 0;
+    for (int i = 0; i < n; ++i) {
+        cnt[i] = (int)floor(slots * w[i] / W);
+        if (cnt[i] < 1) cnt[i] = 1;
+        used += cnt[i];
+    }
+    while (used > slots) {   // rounding up the smallest grids may overshoot
+        int j = 0;
+        for (int i = 1; i < n; ++i) if (cnt[i] > cnt[j]) j = i;
+        --cnt[j];
+        --used;
+    }
+    while (used < slots) {   // the rest to the grids furthest below their share
+        int j = 0;
+        double best = -1e300;
+        for (int i = 0; i < n; ++i) {
+            const double d = slots * w[i] / W - cnt[i];
+            if (d > best) { best = d; j = i; }
+        }
+        ++cnt[j];
+        ++used;
+    }
+    size_t ao = 0;
+    int b0 = 0;
+    for (int i = 0; i < n && rc == TF_OK; ++i) {
+        tf_ctx* h = hs[i];
+        if (!h->primed) {
+            if (launch_prime(h->P, h->stream) != cudaSuccess) rc = TF_ECUDA;
+            h->primed = 1;
+        }
+        Sources S;
+        fill_sources(h, S);
+        if (rc == TF_OK && refresh_order(h, S) != cudaSuccess) rc = TF_ECUDA;
+        BatchGrid& g = G[i];
+        memcpy(&g.tm, h->tmap[0], sizeof(TMaps));
+        g.P[0] = h->P;
+        g.O[0] = h->O;
+        g.P[1] = h->P;
+        g.O[1] = h->O;
+        bind(h, h->cur, h->nxt, g.P[0], g.O[0]);
+        bind(h, h->nxt, h->cur, g.P[1], g.O[1]);
+        g.S = S;
+        g.R = h->R;
+        const int ns = h->nsrc > 0 ? h->nsrc : 1;
+        float* amp = (float*)(amp_host + ao);
+        for (int64_t k = 0; k < nsteps; ++k) {
+            const double t1 = (double)(h->level + k + 1) * h->dt;
+            for (int q = 0; q < h->nsrc; ++q)
+                amp[k * ns + q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
+        }
+        g.amp = (const float*)((char*)scratch + BL.off_amp + ao);
+        ao += align_up(sizeof(float) * (size_t)nsteps * ns);
+        g.level0 = h->level;
+        g.base0 = h->O.base;
+        g.base_inc = counter_advance(h->O.nitems, cnt[i]);
+        g.b0 = b0;
+        g.b1 = b0 + cnt[i];
+        b0 += cnt[i];
+    }
+    int* dstep = (int*)((char*)scratch + BL.off_step);
+    const BatchGrid* dG = (const BatchGrid*)((char*)scratch + BL.off_grids);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (rc == TF_OK && (cudaMemcpyAsync((char*)scratch + BL.off_grids, G, sizeof(BatchGrid) * (size_t)n,
+                                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                        cudaMemcpyAsync((char*)scratch + BL.off_amp, amp_host, BL.bytes - BL.off_amp,
+                                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                        cudaMemsetAsync(dstep, 0, sizeof(int), st) != cudaSuccess))
+        rc = TF_ECUDA;
+    // one launch per step over all grids, K steps captured in a CUDA graph and
+    // replayed (the step number lives on the device; a one-thread launch
+    // advances it after each step), the remaining steps launched directly
+    const int64_t K = nsteps < kBatchGraphSteps ? nsteps : kBatchGraphSteps;
+    if (rc == TF_OK && nsteps >= K && K > 1) {
+        cudaStream_t cs = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            rc = TF_ECUDA;
+        } else {
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            for (int64_t k = 0; k < K && e == cudaSuccess; ++k) {
+                e = launch_step_batch(dG, n, dstep, slots, cs);
+                if (e == cudaSuccess) e = launch_step_advance(dstep, cs);
+            }
+            const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaStreamDestroy(cs);
+            if (e != cudaSuccess) rc = TF_ECUDA;
+        }
+    }
+    int64_t done = 0;
+    if (rc == TF_OK && exec)
+        for (; done + K <= nsteps; done += K)
+            if (cudaGraphLaunch(exec, st) != cudaSuccess) { rc = TF_ECUDA; break; }
+    for (; rc == TF_OK && done < nsteps; ++done)
+        if (launch_step_batch(dG, n, dstep, slots, st) != cudaSuccess || launch_step_advance(dstep, st) != cudaSuccess)
+            rc = TF_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == TF_OK) rc = TF_ECUDA;
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc == TF_OK)
+        for (int i = 0; i < n; ++i) {   // each handle holds the state the run reached
+            tf_ctx* h = hs[i];
+            h->level += nsteps;
+            h->O.base = G[i].base0 + (unsigned long long)nsteps * G[i].base_inc;
+            if (nsteps & 1) {
+                const int t = h->cur;
+                h->cur = h->nxt;
+                h->nxt = t;
+            }
+            const unsigned long long base = h->O.base;
+            bind(h, h->cur, h->nxt, h->P, h->O);
+            h->O.base = base;
+        }
+    free(w); free(cnt); free(G); free(amp_host);
+    return rc;
 }
 
 tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches, int nkinds,

@@ -16,6 +16,7 @@
 // storage grid as the fields; edge and face values are formed in-kernel.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -296,6 +297,28 @@ __device__ __forceinline__ float inv_mu_face(const Params& P, int c, const int p
     const float m1 = __ldg(P.mu + lin(P, q[0], q[1], q[2]));
     return 2.f / (m0 + m1);
 }
+
+// TMA views of the single-step kernel: E box, B box, psi_B box
+struct TMaps {
+    CUtensorMap e, b, pb;
+};
+
+// Batched stepping (tf_batch_run): one launch of the single-step kernel per
+// step over every grid of a batch; each grid owns the CTAs [b0, b1) of the
+// launch.  Per grid, in global memory (written by the host before the run):
+struct __align__(128) BatchGrid {
+    TMaps tm;
+    Params P[2];        // the step from the current buffer (index 0) and from the next one (index 1)
+    StepOut O[2];
+    Sources S;          // amplitudes come from `amp`
+    Probes R;
+    const float* amp;   // [step][source]: amp * s(t^{n+1}) of each step of the run
+    long long level0;   // level at step 0 of the run
+    unsigned long long base0, base_inc;   // counter value at step 0, advance per step
+    int b0, b1;
+};
+cudaError_t launch_step_batch(const BatchGrid* grids, int ngrids, const int* step, int blocks, cudaStream_t st);
+cudaError_t launch_step_advance(int* step, cudaStream_t st);
 
 // launchers (tf_kernels.cu)
 cudaError_t launch_convert_materials(const Params& P, const float* eps_r, const float* mu_r,

@@ -47,6 +47,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <math.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -82,9 +83,6 @@ enum : unsigned {
 };
 constexpr int kFSaxShift = 9;   // staged slab axis + 1 (0: none), two bits
 
-struct TMaps {
-    CUtensorMap e, b, pb;
-};
 
 // the two components != a, ascending (the pair a CPML axis acts on)
 __host__ __device__ __forceinline__ int pair_c1(int a) { return a == 0 ? 1 : 0; }
@@ -263,8 +261,29 @@ __device__ __forceinline__ bool item_is_rare(const Params& P, const Sources& S, 
 
 }  // namespace
 
+// kBatch = false: one grid, its arguments by value.  kBatch = true: one step
+// of a batch of grids (tf_batch_run); the CTA works on the grid whose CTA
+// range holds it, with that grid's arguments from global memory and the step
+// number read from `step_ptr` (so that a captured launch can be replayed).
+template <bool kBatch>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_step(const __grid_constant__ TMaps tm, Params P, StepOut O, Sources S, Probes R, long long level) {
+    k_step_t(const __grid_constant__ TMaps tmk, Params Pk, StepOut Ok, Sources Sk, Probes Rk, long long levelk,
+             const BatchGrid* __restrict__ G, int ngrids, const int* __restrict__ step_ptr) {
+    int gi = 0;
+    if constexpr (kBatch)
+        while (gi + 1 < ngrids && (int)blockIdx.x >= G[gi + 1].b0) ++gi;
+    const BatchGrid* A = G + gi;
+    const int step = kBatch ? __ldg(step_ptr) : 0;
+    const TMaps& tm = kBatch ? A->tm : tmk;
+    const Params& P = kBatch ? A->P[step & 1] : Pk;
+    const StepOut& O = kBatch ? A->O[step & 1] : Ok;
+    const Sources& S = kBatch ? A->S : Sk;
+    const Probes& R = kBatch ? A->R : Rk;
+    const long long level = kBatch ? A->level0 + step : levelk;
+    const unsigned long long obase = kBatch ? A->base0 + (unsigned long long)step * A->base_inc : Ok.base;
+    const int bidx = kBatch ? (int)blockIdx.x - A->b0 : (int)blockIdx.x;
+    const int gdim = kBatch ? A->b1 - A->b0 : (int)gridDim.x;
+    auto amp_of = [&](int s) -> float { return kBatch ? __ldg(A->amp + (long long)step * S.n + s) : S.amp[s]; };
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // TMA destinations must be 128-byte aligned: round the base up (128 spare bytes are allocated)
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
@@ -291,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     // trip does not hold up the producer's warp
     auto ticket = [&]() -> unsigned long long { return atomicAdd(O.ctr, 1ull); };
     auto item_of = [&](unsigned long long tk) -> long long {
-        const long long d = (long long)(tk - O.base) + 2LL * gridDim.x;
+        const long long d = (long long)(tk - obase) + 2LL * gdim;
         return (d >= 0 && d < nitems) ? __ldg(O.order + d) : -1LL;
     };
     // the records of an item: loaded by threads < nq - 1 ...
@@ -391,7 +410,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (tid == kProd) {
         for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const int b = (int)blockIdx.x, g = (int)gridDim.x;
+        if constexpr (kBatch) {
+            // the grid's tensor maps sit in global memory that the host rewrites
+            // between runs: order those writes before the tensor-map proxy reads them
+            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(&tm.e) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(&tm.b) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(&tm.pb) : "memory");
+        }
+        const int b = bidx, g = gdim;
         s_item[0] = b < nitems ? __ldg(O.order + b) : -1LL;
         s_item[1] = (s_item[0] >= 0 && g + b < nitems) ? __ldg(O.order + g + b) : -1LL;
     }
@@ -408,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     // while the ring fills: E^n at the probe points into their DFTs, a probe per CTA
     if (tid < TF_MAX_FREQS)
-        for (int pr = blockIdx.x; pr < R.n; pr += gridDim.x) probe_update(P.E, R, pr, tid, level);
+        for (int pr = bidx; pr < R.n; pr += gdim) probe_update(P.E, R, pr, tid, level);
 
     int cur = 0;
     bool aborted = false;
@@ -806,7 +832,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     float ax0 = 0.f, ax1 = 0.f, ay0 = 0.f, ay1 = 0.f, az0 = 0.f, az1 = 0.f;
                     for (int s = 0; s < S.n; ++s) {
                         if (gy < S.lo[s][1] || gy >= S.hi[s][1] || k < S.lo[s][2] || k >= S.hi[s][2]) continue;
-                        const float v = S.amp[s];
+                        const float v = amp_of(s);
                         const float u0 = (gx0 >= S.lo[s][0] && gx0 < S.hi[s][0]) ? v : 0.f;
                         const float u1 = (gx0 + 1 >= S.lo[s][0] && gx0 + 1 < S.hi[s][0]) ? v : 0.f;
                         const int c = S.comp[s];
@@ -954,17 +980,24 @@ __global__ void k_tile_materials(Params P, float4* rec, int ntx, int nty) {
 
 size_t step_smem_bytes() { return 128 + kStages * sizeof(StageBuf) + 2 * kBPlaneBytes + kStages * 8; }
 
-// opt the kernel in to the dynamic shared memory it needs (above the 48 KB default)
+// opt the kernels in to the dynamic shared memory they need (above the 48 KB default)
 static cudaError_t step_smem_attribute() {
-    return cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute(k_step_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step_t<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem_bytes());
+    return e;
 }
 
 int step_blocks_per_sm() {
     if (step_smem_attribute() != cudaSuccess) return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step, kThreads, step_smem_bytes()) != cudaSuccess)
+    int nb = 0, nb2 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_t<false>, kThreads, step_smem_bytes()) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_step_t<true>, kThreads, step_smem_bytes()) !=
+            cudaSuccess)
         return 0;
-    return nb;
+    return nb < nb2 ? nb : nb2;
 }
 
 cudaError_t make_tensor_map(void* base, const int N[3], int pitch, size_t array_bytes, int narrays, int bx, int by,
@@ -993,7 +1026,32 @@ cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, co
     static cudaError_t attr = step_smem_attribute();
     if (attr != cudaSuccess) return attr;
     const TMaps* tm = (const TMaps*)tmaps;
-    k_step<<<blocks, dim3(kTX, kThreadsY), step_smem_bytes(), st>>>(*tm, P, O, S, R, n);
+    k_step_t<false><<<blocks, dim3(kTX, kThreadsY), step_smem_bytes(), st>>>(*tm, P, O, S, R, n, nullptr, 0, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_batch(const BatchGrid* grids, int ngrids, const int* step, int blocks, cudaStream_t st) {
+    static cudaError_t attr = step_smem_attribute();
+    if (attr != cudaSuccess) return attr;
+    // the by-value arguments are unused in a batched launch
+    TMaps tm;
+    memset(&tm, 0, sizeof(tm));
+    Params P;
+    memset(&P, 0, sizeof(P));
+    StepOut O;
+    memset(&O, 0, sizeof(O));
+    Sources S;
+    memset(&S, 0, sizeof(S));
+    Probes R;
+    memset(&R, 0, sizeof(R));
+    k_step_t<true><<<blocks, dim3(kTX, kThreadsY), step_smem_bytes(), st>>>(tm, P, O, S, R, 0, grids, ngrids, step);
+    return cudaGetLastError();
+}
+
+__global__ void k_step_advance(int* step) { *step += 1; }
+
+cudaError_t launch_step_advance(int* step, cudaStream_t st) {
+    k_step_advance<<<1, 1, 0, st>>>(step);
     return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ EXPORTS = ["tf_workspace_size", "tf_create", "tf_destroy", "tf_storage_dims", "t
            "tf_step_timed", "tf_set_two_step", "tf_two_step_box", "tf_field_stats", "tf_field_stats_noalloc",
            "tf_checkpoint_size",
            "tf_checkpoint_save", "tf_checkpoint_load", "tf_adjoint_scratch_size", "tf_adjoint_run", "tf_batch_step",
+           "tf_batch_scratch_size", "tf_batch_run",
            "tf64_workspace_size", "tf64_create", "tf64_destroy", "tf64_set_materials", "tf64_set_field",
            "tf64_add_source", "tf64_add_probe", "tf64_step", "tf64_sync", "tf64_read_field", "tf64_read_probe_dft",
            "tf64_get_time", "tf64_fma_rate_scratch", "tf64_fma_rate"]
@@ -100,6 +101,8 @@ def load(build_if_missing: bool = True):
                        ("tf_adjoint_scratch_size", [vp, C.c_int64, C.c_int, C.POINTER(C.c_size_t)]),
                        ("tf_adjoint_run", [vp, C.c_int64, C.c_int, C.c_int, C.c_int, vp, C.c_size_t, dp, vp, vp]),
                        ("tf_batch_step", [C.POINTER(vp), C.c_int, C.c_int64]),
+                       ("tf_batch_scratch_size", [C.POINTER(vp), C.c_int, C.c_int64, C.POINTER(C.c_size_t)]),
+                       ("tf_batch_run", [C.POINTER(vp), C.c_int, C.c_int64, dp, vp, C.c_size_t]),
                        ("tf64_create", [C.POINTER(tf_grid_desc), vp, C.c_size_t, C.POINTER(vp)]),
                        ("tf64_destroy", [vp]), ("tf64_set_materials", [vp, vp, vp, vp, vp]),
                        ("tf64_set_field", [vp, C.c_int, vp]),
@@ -316,6 +319,27 @@ def batch_step(grids, nsteps: int):
     _check(load().tf_batch_step(hs, len(grids), int(nsteps)), "tf_batch_step")
 
 
+def batch_run(grids, nsteps: int, weights=None):
+    """Advance every grid of `grids` by nsteps with one launch per step over
+    all of them (tf_batch_run), the steps replayed from a CUDA graph; CTAs
+    are split among the grids by `weights` (e.g. measured ms per step) or by
+    cells with CPML cells counted 2.5 times.  Synchronises."""
+    import torch
+    hs = (C.c_void_p * len(grids))(*[g.h for g in grids])
+    n = C.c_size_t()
+    _check(load().tf_batch_scratch_size(hs, len(grids), int(nsteps), C.byref(n)), "tf_batch_scratch_size")
+    scratch = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=grids[0].device)
+    base = int(scratch.data_ptr())
+    off = (-base) % 256
+    wp = None
+    if weights is not None:
+        wa = np.ascontiguousarray(np.asarray(weights, np.float64))
+        wp = wa.ctypes.data_as(C.POINTER(C.c_double))
+    _check(load().tf_batch_run(hs, len(grids), int(nsteps), wp, C.c_void_p(base + off), int(n.value)),
+           "tf_batch_run")
+    del scratch
+
+
 def _ptr(buf):
     """(pointer, on_device) of a numpy array or a CUDA torch tensor."""
     if isinstance(buf, np.ndarray):
@@ -442,9 +466,13 @@ class Grid:
         kt = {names[k]: (ms[k], int(cnt[k])) for k in range(3) if cnt[k]}
         return (kt, tot.value) if with_total else kt
 
-    def set_two_step(self, enable: bool):
-        """Allow (default) or forbid two-step passes (temporal blocking)."""
-        _check(load().tf_set_two_step(self.h, 1 if enable else 0), "tf_set_two_step")
+    def set_two_step(self, planes):
+        """Two-step passes (temporal blocking): False / 0 forbids them, True
+        allows them with 16-plane work items (the default), 4 .. 16 sets the
+        work-item length."""
+        if planes is True:
+            planes = 16
+        _check(load().tf_set_two_step(self.h, int(planes or 0)), "tf_set_two_step")
 
     def two_step_box(self):
         """((lo, hi) of the two-step box in storage points per axis, active)."""

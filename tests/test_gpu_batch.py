@@ -42,3 +42,72 @@ def test_batch_rejects_a_handle_twice():
     with pytest.raises(tf.TFError) as ex:
         tf.batch_step([g, g], 1)
     assert ex.value.status == tf.TF_EINVAL
+
+
+def test_batch_run_one_launch_per_step_matches_single_grids():
+    """tf_batch_run (one launch per step over all grids, 64 steps per CUDA
+    graph): every grid bit-identical to stepping it alone, over a step count
+    that is not a multiple of the graph's 64 steps, with the heuristic CTA
+    split and with explicit weights."""
+    from paper_2305_13419_gb300 import twofluid as tf
+    ws = _variants()
+    refs = []
+    for w in ws:
+        ref = tf.Grid.from_workload(w)
+        ref.step(150)
+        ref.sync()
+        refs.append(ref)
+    for weights in (None, [1.0 + i for i in range(len(ws))]):
+        batch = [tf.Grid.from_workload(w) for w in ws]
+        batch[0].step(3)   # grids at different levels and buffer parities
+        tf.batch_run(batch[1:], 3)
+        tf.batch_run(batch, 147, weights)
+        for w, g, ref in zip(ws, batch, refs):
+            g.sync()
+            assert g.level == 150
+            for c in range(9):
+                assert np.array_equal(g.field(c), ref.field(c)), (w.name, c)
+            for p in range(len(w.probes)):
+                assert np.array_equal(g.probe_dft(p), ref.probe_dft(p))
+        # the handles keep stepping on their own afterwards
+        more = tf.Grid.from_workload(ws[2])
+        more.step(155)
+        batch[2].step(5)
+        assert np.array_equal(batch[2].field(0), more.field(0))
+
+
+def test_batch_run_grids_against_the_oracle():
+    """Three CPW variants of the batched workload's recipe (uneven sizes,
+    strip / gap widths, lambda_L) advanced by tf_batch_run, each against the
+    FP64 oracle: fields within 1e-4 relative L2, probe spectra within 1e-3."""
+    from paper_2305_13419_gb300 import twofluid as tf
+    from parity_util import SPEC_TOL, compare_fields, rel_l2, run_oracle
+    ws = W.cpw_batch(count=3, seed=23, sizes=(40, 48, 64))
+    grids = [tf.Grid.from_workload(w) for w in ws]
+    tf.batch_run(grids, 200)
+    for w, g in zip(ws, grids):
+        g.sync()
+        go = run_oracle(w, 200)
+        errs, bad = compare_fields(g, go)
+        assert not bad, (w.name, errs)
+        for p in range(len(w.probes)):
+            assert rel_l2(g.probe_dft(p), go.probe_dft(p)) < SPEC_TOL, (w.name, p)
+
+
+def test_batch_run_rejects_bad_calls():
+    import ctypes as C
+    from paper_2305_13419_gb300 import twofluid as tf
+    g = tf.Grid.from_workload(_variants()[0])
+    with pytest.raises(tf.TFError) as ex:
+        tf.batch_run([g, g], 1)
+    assert ex.value.status == tf.TF_EINVAL
+    with pytest.raises(tf.TFError) as ex:
+        tf.batch_run([g], 1, weights=[0.0])
+    assert ex.value.status == tf.TF_EINVAL
+    hs = (C.c_void_p * 1)(g.h)
+    n = C.c_size_t()
+    assert tf.load().tf_batch_scratch_size(hs, 1, 10, C.byref(n)) == tf.TF_OK
+    buf = torch.empty(int(n.value) + 512, dtype=torch.uint8, device="cuda")
+    p = (int(buf.data_ptr()) + 255) // 256 * 256
+    assert tf.load().tf_batch_run(hs, 1, 10, None, C.c_void_p(p), int(n.value) - 1) == tf.TF_ENOMEM
+    assert tf.load().tf_batch_run(hs, 1, 10, None, C.c_void_p(p + 4), int(n.value)) == tf.TF_EINVAL
