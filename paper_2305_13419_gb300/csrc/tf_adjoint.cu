@@ -85,8 +85,12 @@ __global__ void __launch_bounds__(kAX * kAY) k_adj_faces(Params P, AdjState A) {
 }
 
 // edge pass: Jh, psi_Eh, Eh; per-edge gradients; the objective's derivative
-// at the probe; the edge weights of the next step
-__global__ void __launch_bounds__(kAX * kAY) k_adj_edges(Params P, AdjState A, Sources S, AdjStep st) {
+// at the probe; the edge weights of the next step.  The step's coefficients
+// are the ones the forward step used: the tile-plane record where the
+// material of the tile-plane is uniform, else the per-point arrays; (1, 0, 0)
+// on edges the step leaves alone.
+__global__ void __launch_bounds__(kAX * kAY) k_adj_edges(Params P, AdjState A, Sources S, AdjStep st,
+                                                        const float4* __restrict__ tilemat, int ntx) {
     int p[3];
     if (!point_of(P, p)) return;
     const int q = lin32(P, p[0], p[1], p[2]);
@@ -96,6 +100,13 @@ __global__ void __launch_bounds__(kAX * kAY) k_adj_edges(Params P, AdjState A, S
     const bool hp[3] = {P.per[0] || p[0] > 0, P.per[1] || p[1] > 0, P.per[2] || p[2] > 0};
     const bool in_src = S.n > 0 && p[0] >= S.bb_lo[0] && p[0] <= S.bb_hi[0] && p[1] >= S.bb_lo[1] &&
                         p[1] <= S.bb_hi[1] && p[2] >= S.bb_lo[2] && p[2] <= S.bb_hi[2];
+    // the forward step's record of this point's tile-plane (points past the
+    // last tile of a walled axis are walls: no record needed)
+    const int tx = p[0] / kSX, ty = p[1] / kSY;
+    const bool intile = p[0] < (P.per[0] ? P.N[0] : P.n[0]) && p[1] < (P.per[1] ? P.N[1] : P.n[1]);
+    const float4 rec = intile ? __ldg(tilemat + (long long)(ty * ntx + tx) * P.N[2] + p[2])
+                              : make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+    const bool uni = !isnan(rec.x);
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         const float ep = A.E[e][q];
@@ -108,10 +119,11 @@ __global__ void __launch_bounds__(kAX * kAY) k_adj_edges(Params P, AdjState A, S
             if (hp[a]) d += A.U[c][a][qp[a]];
             d -= A.U[c][a][q];
         }
-        const float cb = __ldg(P.cb[e] + q);
+        const bool upd = upd_E(P, e, p);
+        const float cb = !upd ? 0.f : uni ? rec.y : __ldg(P.cb[e] + q);
         float enew = ep + d;
         if (cb != 0.f) {
-            const float ev = cb * ep, cj = __ldg(P.cj[e] + q);
+            const float ev = cb * ep, cj = uni ? rec.z : __ldg(P.cj[e] + q);
             const float jh = A.J[e][q] - ev;
             A.J[e][q] = jh;
 #pragma unroll
@@ -119,7 +131,7 @@ __global__ void __launch_bounds__(kAX * kAY) k_adj_edges(Params P, AdjState A, S
                 if (a == e || !A.psiE[e][a] || !in_slab(P, a, p[a])) continue;
                 A.psiE[e][a][q] = __ldg(P.pbE[a] + p[a]) * (A.psiE[e][a][q] + curl_sign(e, a) * ev);
             }
-            enew = __ldg(P.ca[e] + q) * ep + cj * jh + d;
+            enew = (uni ? rec.x : __ldg(P.ca[e] + q)) * ep + cj * jh + d;
             // gradients: E^n, and E^{n+1} without this step's soft sources
             const float en = st.En[e][q];
             float e1 = st.En1[e][q];
@@ -227,10 +239,10 @@ cudaError_t launch_copy3(float* const dst[3], float* const src[3], long long n, 
 }
 
 cudaError_t launch_adjoint_step(const Params& P, const AdjState& A, const Sources& S, const AdjStep& st,
-                                cudaStream_t stream) {
+                                const float4* tilemat, int ntx, cudaStream_t stream) {
     const dim3 grid((P.N[0] + kAX - 1) / kAX, (P.N[1] + kAY - 1) / kAY, P.N[2]), block(kAX, kAY);
     k_adj_faces<<<grid, block, 0, stream>>>(P, A);
-    k_adj_edges<<<grid, block, 0, stream>>>(P, A, S, st);
+    k_adj_edges<<<grid, block, 0, stream>>>(P, A, S, st, tilemat, ntx);
     return cudaGetLastError();
 }
 

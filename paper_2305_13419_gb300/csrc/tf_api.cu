@@ -99,7 +99,8 @@ Layout layout_of(const tf_grid_desc* d) {
     // two-step box cuts them, each chunk in pieces at most
     L.max_s = (long long)L.ntx * L.nty * (L.nch + 2) * ((kChunk + kSub - 1) / kSub);
     L.off_order_s = o; o += align_up(sizeof(long long) * (size_t)L.max_s);
-    L.max_t = (long long)L.ntx * L.nty * (L.N[2] / kTBLenMax + 1);
+    // box list: its tiles in items of at least kTBLenMin planes
+    L.max_t = (long long)L.ntx * L.nty * (L.N[2] / kTBLenMin + 1);
     L.off_order_t = o; o += align_up(sizeof(long long) * (size_t)L.max_t);
     L.off_stats = o;  o += align_up(sizeof(StatPartial) * (size_t)(L.N[2] + 1));
     L.off_misc = o;   o += kAlign;
@@ -712,6 +713,7 @@ cudaError_t build_two_step_lists(tf_ctx* h, const Sources& S) {
         return cudaErrorMemoryAllocation;
     }
     long long ns = 0, nf = 0, nt = 0, npieces = 0;
+    bool ok = true;
     for (int pass = 0; pass < 2; ++pass) {   // pass 0 counts the pieces, pass 1 lists them
         const bool split = pass == 1 && npieces < 8LL * h->slots;
         for (int kz = 0; kz < L.kend; kz += kChunk) {
@@ -729,6 +731,7 @@ cudaError_t build_two_step_lists(tf_ctx* h, const Sources& S) {
                     for (int p = 0; p < np; ++p) {
                         if (hi[p] <= lo[p]) continue;
                         if (pass == 0) { ++npieces; continue; }
+                        if (ns + nf + (hi[p] - lo[p]) > L.max_s) { ok = false; continue; }   // never: sized for it
                         if (rare_item(h, S, tile, lo[p], hi[p] - lo[p])) {
                             const int piece = split ? kSub : hi[p] - lo[p];
                             for (int k = lo[p]; k < hi[p]; k += piece)
@@ -743,17 +746,28 @@ cudaError_t build_two_step_lists(tf_ctx* h, const Sources& S) {
     // the last plain items, one per CTA slot, go out in kSub-plane pieces
     const long long cut = nf > h->slots ? nf - h->slots : 0;
     for (long long i = 0; i < cut; ++i) sl[ns++] = fa[i];
-    for (long long i = cut; i < nf; ++i) {
+    for (long long i = cut; i < nf && ok; ++i) {
         const long long d = fa[i];
         const int tile = item_tile(d), kz0 = item_kz0(d), len = item_len(d);
-        for (int k = kz0; k < kz0 + len; k += kSub)
+        for (int k = kz0; k < kz0 + len; k += kSub) {
+            if (ns >= L.max_s) { ok = false; break; }
             sl[ns++] = make_item(tile, k, (kz0 + len - k) < kSub ? kz0 + len - k : kSub);
+        }
     }
     for (int kz = h->tz0; kz < h->tz1; kz += h->tb_len) {
         const int len = h->tz1 - kz < h->tb_len ? h->tz1 - kz : h->tb_len;
         for (int ty = h->ty0; ty < h->ty1; ++ty)
-            for (int tx = h->tx0; tx < h->tx1; ++tx)
+            for (int tx = h->tx0; tx < h->tx1; ++tx) {
+                if (nt >= L.max_t) { ok = false; break; }
                 tl[nt++] = make_item(ty * L.ntx + tx, kz, len);
+            }
+    }
+    if (!ok) {   // a list outgrew its region: no two-step passes (never expected)
+        free(sl);
+        free(fa);
+        free(tl);
+        h->nitems_s = h->nitems_t = 0;
+        return cudaErrorInvalidValue;
     }
     cudaError_t e = cudaSuccess;
     if (ns > 0)
@@ -829,7 +843,7 @@ tf_status tf_step(tf_handle h, int64_t nsteps) {
 }
 
 tf_status tf_set_two_step(tf_handle h, int planes) {
-    if (!h || (planes != 0 && (planes < 4 || planes > kTBLenMax))) return TF_EINVAL;
+    if (!h || (planes != 0 && (planes < kTBLenMin || planes > kTBLenMax))) return TF_EINVAL;
     h->two_step_on = planes != 0;
     if (planes != 0 && planes != h->tb_len) {
         h->tb_len = planes;
@@ -1470,7 +1484,7 @@ tf_status tf_adjoint_run(tf_handle h, int64_t nsteps, int probe, int freq_index,
             }
             const double t1 = (double)(n + 1) * h->dt;
             for (int q = 0; q < h->nsrc; ++q) src.amp[q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
-            TF_CUDA(launch_adjoint_step(h->P, S, src, st, h->stream));
+            TF_CUDA(launch_adjoint_step(h->P, S, src, st, h->O.tilemat, h->L.ntx, h->stream));
         }
     }
     TF_CUDA(launch_adjoint_cells(h->P, S, (float)(kC0 * h->dt), 1.0 / seed_scale, grad_eps, grad_lambda,

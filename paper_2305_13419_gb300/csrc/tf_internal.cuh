@@ -157,7 +157,7 @@ struct Probes {
 // n+1 E / n+1/2 B of the points within two of the box faces (and of probe
 // points) to the third buffer, from which the single-step kernel advances
 // the rest of the grid to level n+2.
-constexpr int kTBLenMax = 16;   // planes per two-step work item
+constexpr int kTBLenMax = 16, kTBLenMin = 4;   // planes per two-step work item (the default is the maximum)
 struct Step2Out {
     float* E[3];             // E^{n+2}, B^{n+3/2}, Jt^{n+3/2}
     float* B[3];
@@ -364,7 +364,7 @@ struct AdjStep {
     float probe_src;
 };
 cudaError_t launch_adjoint_step(const Params& P, const AdjState& A, const Sources& S, const AdjStep& st,
-                                cudaStream_t stream);
+                                const float4* tilemat, int ntx, cudaStream_t stream);
 // copy three float arrays of n elements (n a multiple of 4, 16-byte aligned)
 cudaError_t launch_copy3(float* const dst[3], float* const src[3], long long n, cudaStream_t stream);
 cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0, double unscale, float* g_eps,

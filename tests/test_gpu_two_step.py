@@ -91,3 +91,23 @@ def test_non_uniform_mu_keeps_single_steps():
     assert not active and all(hi[a] > lo[a] for a in range(3))
     kt = g.step_timed(4)
     assert "step2" not in kt and kt["step"][1] == 4
+
+
+@pytest.mark.parametrize("planes", [4, 7, 12])
+def test_two_step_item_lengths_give_the_same_bits(planes):
+    """The autotuner's knob: every two-step work-item length gives the bits
+    of single steps; lengths outside 4 .. 16 are rejected."""
+    from paper_2305_13419_gb300 import twofluid as tf
+    w = _cpw_with_inner_source()
+    ref = _run(w, False, [21], None)
+    g = tf.Grid.from_workload(w)
+    g.set_two_step(planes)
+    g.step(21)
+    g.sync()
+    assert g.two_step_box()[1]
+    for c in range(9):
+        assert np.array_equal(g.field(c), ref.field(c)), c
+    for bad in (1, 3, 17):
+        with pytest.raises(tf.TFError) as ex:
+            g.set_two_step(bad)
+        assert ex.value.status == tf.TF_EINVAL
