@@ -436,12 +436,7 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.no_adjoint:
         adj = run_adjoint(args)
     if rank == 0 and not args.no_batch:
-        weights = None
-        if not args.no_autotune:   # CTA shares of the batch from each grid's measured step time
-            from paper_2305_13419_gb300 import autotune
-            from paper_2305_13419_gb300 import workloads as W
-            weights = autotune.batch_weights(W.cpw_batch(), steps=10)
-        batch = run_batch(args, plain_small or value / ws, weights)
+        batch = run_batch(args, plain_small or value / ws)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -467,13 +462,19 @@ def run_adjoint(args):
     from paper_2305_13419_gb300 import workloads as W
     w = W.cpw_adjoint(nsteps=args.adjoint_steps)
     g = tf.Grid.from_workload(w)
+    tuning = None
+    if not args.no_autotune:   # the plain step at its best setting; the adjoint's forward runs use it too
+        from paper_2305_13419_gb300 import autotune
+        tuning = autotune.tune_grid(g, steps=args.autotune_steps)
     g.step(20)
-    kt = g.step_timed(200)
+    _, tot = g.step_timed(200, with_total=True)
     g.sync()
-    plain = sum(v[0] for v in kt.values())
+    plain = tot / 200
     g.close()
     del g
     g = tf.Grid.from_workload(w)
+    if tuning is not None:
+        g.set_two_step(tuning["best"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     J, ge, gl = g.adjoint(args.adjoint_steps, 0, 0, segment=args.adjoint_segment)
@@ -482,18 +483,18 @@ def run_adjoint(args):
     per = ms / args.adjoint_steps
     return {"workload": w.name, "steps": args.adjoint_steps, "segment": args.adjoint_segment, "ms": ms,
             "ms_per_step": per,
-            "plain_ms_per_step": plain, "vs_plain_step": per / plain,
+            "plain_ms_per_step": plain, "vs_plain_step": per / plain, "autotune": tuning,
             "gcell_updates_per_s": w.ncells * args.adjoint_steps / (ms * 1e-3) / 1e9,
             "objective": J, "grad_eps_absmax": float(ge.abs().max()), "grad_lambda_absmax": float(gl.abs().max()),
             "includes": "forward with checkpoints, per-segment recompute, adjoint steps, gradient reduction"}
 
 
-def run_batch(args, plain_gcells, weights=None):
+def run_batch(args, plain_gcells):
     """The batched workload: 64 CPW variants with axes from {96, 128, 160}.
-    Headline: tf_batch_run, one launch per step over all 64 grids (CTAs split
-    among the grids by `weights`, else by cells with CPML cells counted 2.5
-    times), 64 steps per CUDA graph, timed with CUDA events on its stream;
-    beside it tf_batch_step (per-grid launches spread over 8 streams)."""
+    Headline: tf_batch_run, one launch per step over all 64 grids (one work
+    list over all grids' items), 64 steps per CUDA graph, timed with CUDA
+    events on its stream; beside it tf_batch_step (per-grid launches spread
+    over 8 streams)."""
     import time
     import torch
     from paper_2305_13419_gb300 import twofluid as tf
@@ -502,12 +503,12 @@ def run_batch(args, plain_gcells, weights=None):
     cells = sum(w.ncells for w in ws)
     out = {"grids": len(ws), "cells": cells, "steps": args.batch_steps, "sizes": [96, 128, 160]}
     grids = [tf.Grid.from_workload(w) for w in ws]
-    tf.batch_run(grids, 10, weights)
+    tf.batch_run(grids, 10)
     torch.cuda.synchronize()
     st = grids[0].stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    tf.batch_run(grids, args.batch_steps, weights)
+    tf.batch_run(grids, args.batch_steps)
     e1.record(st)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -518,7 +519,6 @@ def run_batch(args, plain_gcells, weights=None):
     torch.cuda.empty_cache()
     out["one_launch"] = {"ms_per_step": ms / args.batch_steps,
                          "gcell_updates_per_s": cells * args.batch_steps / (ms * 1e-3) / 1e9,
-                         "weights": "autotuned" if weights is not None else "cells, CPML cells x 2.5",
                          "timing": "CUDA events on the batch's stream around tf_batch_run (includes its set-up "
                                    "uploads and graph capture)"}
     streams = [torch.cuda.Stream() for _ in range(8)]
@@ -687,6 +687,19 @@ def run_precision_study(args):
     return 0
 
 
+def run_autotune_table(args):
+    """The autotuner over every workload class of the study: temporal-block
+    depth and two-step item length per class, from measured runs; writes the
+    table to --autotune-table and prints it as one JSON line."""
+    from paper_2305_13419_gb300 import autotune
+    from paper_2305_13419_gb300 import workloads as W
+    ws = [W.slab(), W.cpw(), W.cpw_adjoint(), W.cpw_large(nsteps=10)] + W.cpw_batch()
+    table = autotune.tune_classes(ws, steps=args.autotune_steps)
+    autotune.save(table, args.autotune_table)
+    print(json.dumps({"autotune_table": table}), flush=True)
+    return 0
+
+
 def run_e2e(args, w, dev):
     """Same metric through the public API from host memory: the timed region
     uploads the material maps from pinned host buffers, runs the K steps and
@@ -732,6 +745,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--cpw-steps", type=int, default=2000, help="steps of the 512 x 256 x 128 CPW line")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default settings")
+    ap.add_argument("--autotune-table", default="",
+                    help="tune every workload class (slab, CPWs, adjoint grid, the batch's size classes) and "
+                         "write the table to this JSON path (one JSON line printed)")
     ap.add_argument("--autotune-steps", type=int, default=20, help="steps timed per autotuner candidate")
     ap.add_argument("--workload", choices=("large", "cpw"), default="large",
                     help="the timed workload: the 1024 x 512 x 256 CPW (default) or the 512 x 256 x 128 one")
@@ -772,6 +788,8 @@ def main(argv=None):
         return 0
     if args.fp64_study > 0:
         return run_precision_study(args)
+    if args.autotune_table:
+        return run_autotune_table(args)
     if args.all_configs:
         return run_all_configs(args)
     return run_ours(args, ws, rank, local)

@@ -208,24 +208,24 @@ tf_status tf_two_step_box(tf_handle h, int lo[3], int hi[3], int* active);
 tf_status tf_batch_step(const tf_handle* hs, int n, int64_t nsteps);
 
 /* One launch per step over every grid of a batch (many resonator variants
- * of uneven sizes): the single-step kernel's CTAs are split among the grids
- * in proportion to their work (`weights`, e.g. an autotuner's measured times
- * per step, or NULL for cells with CPML slab cells counted 2.5 times), each
- * CTA takes work items of its grid only, and 64 steps at a time are captured
- * in a CUDA graph and replayed (the step number lives on the device and a
- * one-thread launch advances it after each step).  Every grid ends with the
- * same bits as tf_step (single steps) would give it.
- *   hs, n      handles (distinct, n <= the CTA slots of the device, else
- *              TF_ENOTSUP); the run is issued on hs[0]'s stream after every
- *              handle's stream has been synchronised, and synchronises it;
- *   weights    n positive numbers or NULL;
+ * of uneven sizes): the work items of all grids form one list (each grid's
+ * own items, the grid's index in the descriptor; the items with CPML
+ * corners, sources or Mur planes of every grid first) that the single-step
+ * kernel's CTAs share through one counter, each item run with its grid's
+ * arguments; 64 steps at a time are captured in a CUDA graph and replayed
+ * (the step number lives on the device and a one-thread launch advances it
+ * after each step).  Every grid ends with the same bits as tf_step (single
+ * steps) would give it.
+ *   hs, n      handles (distinct, n <= 32768); the run is issued on hs[0]'s
+ *              stream after every handle's stream has been synchronised, and
+ *              synchronises it;
  *   scratch    caller-owned device memory (256-byte aligned) of at least
- *              tf_batch_scratch_size bytes: the per-grid arguments and the
- *              source amplitudes of every step (TF_ENOMEM if smaller).
+ *              tf_batch_scratch_size bytes: the per-grid arguments, the work
+ *              list and the source amplitudes of every step (TF_ENOMEM if
+ *              smaller).
  * Creating the CUDA graph may make the CUDA runtime allocate. */
 tf_status tf_batch_scratch_size(const tf_handle* hs, int n, int64_t nsteps, size_t* bytes);
-tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, const double* weights, void* scratch,
-                       size_t bytes);
+tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, void* scratch, size_t bytes);
 
 /* Wait for the stream and return the latched device status
  * (TF_ENONFINITE if the watchdog saw a non-finite E). */

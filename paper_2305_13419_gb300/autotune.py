@@ -1,14 +1,15 @@
 """The project's autotuner: picks, from measured runs on the GPU, the runtime
-settings of libtwofluid for a grid and the CTA split of a batch.
+settings of libtwofluid per grid and per class of grids.
 
 Every setting gives the same bits (the step's arithmetic does not depend on
 how the work is cut), so the tuner only times.  What it chooses:
 
   * temporal-block depth per grid: single steps (T = 1) or two steps per
     pass over the interior box (T = 2) with two-step work items of 8, 12 or
-    16 planes (tf_set_two_step);
-  * for a batch (tf_batch_run): the share of the launch's CTAs each grid
-    gets, in proportion to its measured time per step when stepped alone.
+    16 planes (tf_set_two_step).
+
+A batch (tf_batch_run) needs no split to tune: its grids' work items form
+one list that the launch's CTAs share through one counter.
 
 The tile shape (32 x 16 columns, 8-plane single-step items) is fixed when the
 kernels are compiled; the shapes measured against it are listed in the
@@ -17,7 +18,7 @@ design notes.  Results are plain dicts, written to JSON by `save`.
 from __future__ import annotations
 
 import json
-from typing import Dict, Iterable, List, Sequence
+from typing import Dict, Iterable
 
 TWO_STEP_CANDIDATES = (0, 8, 12, 16)   # 0: single steps; else planes per two-step work item
 
@@ -49,21 +50,33 @@ def tune_grid(grid, steps: int = 20, warmup: int = 4, candidates: Iterable[int] 
     return {"best": best, "ms_per_step": table, "interior_box": [list(lo), list(hi)] if usable else None}
 
 
-def batch_weights(workloads: Sequence, steps: int = 20, warmup: int = 3, device=None) -> List[float]:
-    """Measured ms per single step of each workload's grid stepped alone: the
-    CTA weights of tf_batch_run."""
+def grid_class(w) -> str:
+    """Class of a workload for tuning: its cell counts and boundary kinds."""
+    return "x".join(map(str, w.n)) + "-" + "-".join(w.bc)
+
+
+def tune_classes(workloads, steps: int = 20, device=None) -> Dict:
+    """Tunes one grid per class of `workloads` (the first of each class) and
+    returns {class: tune_grid result}, ready for `save`."""
     import torch
     from . import twofluid as tf
-    out = []
+    table = {}
     for w in workloads:
+        key = grid_class(w)
+        if key in table:
+            continue
         g = tf.Grid.from_workload(w, device=device)
-        g.set_two_step(0)
-        g.step(warmup)
-        out.append(_time_steps(g, steps))
+        table[key] = tune_grid(g, steps=steps)
         g.close()
         del g
         torch.cuda.empty_cache()
-    return out
+    return table
+
+
+def setting_for(table: Dict, w, default: int = 16) -> int:
+    """The tuned two-step setting of a workload's class (default if untuned)."""
+    r = table.get(grid_class(w))
+    return int(r["best"]) if r else default
 
 
 def save(table: Dict, path: str) -> None:

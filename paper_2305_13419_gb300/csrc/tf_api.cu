@@ -906,14 +906,23 @@ namespace {
 constexpr int kBatchGraphSteps = 64;   // steps per captured graph
 
 struct BatchLayout {
-    size_t off_step, off_grids, off_amp, bytes;
+    size_t off_step, off_grids, off_probes, off_order, off_amp, bytes;
+    long long max_items;
 };
+
+long long order_capacity(const tf_ctx* h) {
+    return (long long)h->L.ntx * h->L.nty * h->L.nch * ((kChunk + kSub - 1) / kSub);
+}
 
 BatchLayout batch_layout(const tf_handle* hs, int n, int64_t nsteps) {
     BatchLayout B{};
     size_t o = 0;
-    B.off_step = o;  o += kAlign;
-    B.off_grids = o; o += align_up(sizeof(BatchGrid) * (size_t)n);
+    B.off_step = o;   o += kAlign;   // step number, work counter
+    B.off_grids = o;  o += align_up(sizeof(BatchGrid) * (size_t)n);
+    B.off_probes = o; o += align_up(sizeof(int) * 2 * TF_MAX_PROBES * (size_t)n);
+    B.max_items = 0;
+    for (int i = 0; i < n; ++i) B.max_items += order_capacity(hs[i]);
+    B.off_order = o;  o += align_up(sizeof(long long) * (size_t)B.max_items);
     B.off_amp = o;
     for (int i = 0; i < n; ++i) o += align_up(sizeof(float) * (size_t)nsteps * (size_t)(hs[i]->nsrc > 0 ? hs[i]->nsrc : 1));
     B.bytes = o;
@@ -940,77 +949,54 @@ tf_status tf_batch_scratch_size(const tf_handle* hs, int n, int64_t nsteps, size
     return TF_OK;
 }
 
-tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, const double* weights, void* scratch,
-                       size_t bytes) {
+tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, void* scratch, size_t bytes) {
     tf_status rc = batch_check(hs, n, nsteps);
     if (rc != TF_OK) return rc;
     if (!scratch || ((uintptr_t)scratch) % kAlign) return TF_EINVAL;
     const BatchLayout BL = batch_layout(hs, n, nsteps);
     if (bytes < BL.bytes) return TF_ENOMEM;
     if (nsteps == 0) return TF_OK;
-    const int slots = hs[0]->slots;
-    if (n > slots) return TF_ENOTSUP;   // every grid needs a CTA of its own
-    if (weights)
-        for (int i = 0; i < n; ++i)
-            if (!(weights[i] > 0) || !isfinite(weights[i])) return TF_EINVAL;
+    if (n > (1 << 15)) return TF_ENOTSUP;   // the grid index fills descriptor bits 48-62
     // the grids' earlier work is done before the batch reads their state
     for (int i = 0; i < n; ++i) TF_CUDA(cudaStreamSynchronize(hs[i]->stream));
     cudaStream_t st = hs[0]->stream;
-    // CTAs per grid in proportion to its work: the caller's weights (an
-    // autotuner's measured times per step), else cells with CPML slab cells counted 2.5 times
-    double* w = (double*)malloc(sizeof(double) * (size_t)n);
-    int* cnt = (int*)malloc(sizeof(int) * (size_t)n);
+    const int slots = hs[0]->slots;
     BatchGrid* G = (BatchGrid*)calloc((size_t)n, sizeof(BatchGrid));
     char* amp_host = (char*)malloc(BL.bytes - BL.off_amp);
-    if (!w || !cnt || !G || !amp_host) {
-        free(w); free(cnt); free(G); free(amp_host);
+    long long* items = (long long*)malloc(sizeof(long long) * (size_t)BL.max_items);
+    long long* list = (long long*)malloc(sizeof(long long) * (size_t)BL.max_items);
+    char* rare = (char*)malloc((size_t)BL.max_items);
+    int* probes = (int*)malloc(sizeof(int) * 2 * TF_MAX_PROBES * (size_t)n);
+    if (!G || !amp_host || !items || !list || !rare || !probes) {
+        free(G); free(amp_host); free(items); free(list); free(rare); free(probes);
         return TF_ENOMEM;
     }
-    double W = 0.0;
-    for (int i = 0; i < n; ++i) {
-        const tf_ctx* h = hs[i];
-        if (weights) {
-            w[i] = weights[i];
-        } else {
-            double inner = 1.0;
-            for (int a = 0; a < 3; ++a) inner *= 1.0 - 2.0 * h->P.L[a] / (double)h->P.n[a];
-            w[i] = (double)h->L.ncell * (1.0 + 1.5 * (1.0 - inner));
-        }
-        W += w[i];
-    }
-    int used = 0;
-    for (int i = 0; i < n; ++i) {
-        cnt[i] = (int)floor(slots * w[i] / W);
-        if (cnt[i] < 1) cnt[i] = 1;
-        used += cnt[i];
-    }
-    while (used > slots) {   // rounding up the smallest grids may overshoot
-        int j = 0;
-        for (int i = 1; i < n; ++i) if (cnt[i] > cnt[j]) j = i;
-        --cnt[j];
-        --used;
-    }
-    while (used < slots) {   // the rest to the grids furthest below their share
-        int j = 0;
-        double best = -1e300;
-        for (int i = 0; i < n; ++i) {
-            const double d = slots * w[i] / W - cnt[i];
-            if (d > best) { best = d; j = i; }
-        }
-        ++cnt[j];
-        ++used;
-    }
+    // one work list over all grids: each grid's items (its own order) with
+    // the grid's index in the descriptor; the items that take the full plane
+    // body, of every grid, first
+    long long ntot = 0, nrare = 0;
+    int np = 0;
     size_t ao = 0;
-    int b0 = 0;
     for (int i = 0; i < n && rc == TF_OK; ++i) {
         tf_ctx* h = hs[i];
         if (!h->primed) {
-            if (launch_prime(h->P, h->stream) != cudaSuccess) rc = TF_ECUDA;
+            if (launch_prime(h->P, h->stream) != cudaSuccess) { rc = TF_ECUDA; break; }
             h->primed = 1;
         }
         Sources S;
         fill_sources(h, S);
-        if (rc == TF_OK && refresh_order(h, S) != cudaSuccess) rc = TF_ECUDA;
+        if (refresh_order(h, S) != cudaSuccess ||
+            cudaMemcpy(items + ntot, h->O.order, sizeof(long long) * (size_t)h->O.nitems, cudaMemcpyDeviceToHost) !=
+                cudaSuccess) {
+            rc = TF_ECUDA;
+            break;
+        }
+        for (long long k = ntot; k < ntot + h->O.nitems; ++k) {
+            rare[k] = rare_item(h, S, item_tile(items[k]), item_kz0(items[k]), item_len(items[k])) ? 1 : 0;
+            items[k] = item_with_grid(items[k], i);
+            nrare += rare[k];
+        }
+        ntot += h->O.nitems;
         BatchGrid& g = G[i];
         memcpy(&g.tm, h->tmap[0], sizeof(TMaps));
         g.P[0] = h->P;
@@ -1031,34 +1017,51 @@ tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, const double*
         g.amp = (const float*)((char*)scratch + BL.off_amp + ao);
         ao += align_up(sizeof(float) * (size_t)nsteps * ns);
         g.level0 = h->level;
-        g.base0 = h->O.base;
-        g.base_inc = counter_advance(h->O.nitems, cnt[i]);
-        g.b0 = b0;
-        g.b1 = b0 + cnt[i];
-        b0 += cnt[i];
+        for (int p = 0; p < h->R.n; ++p) {
+            probes[2 * np] = i;
+            probes[2 * np + 1] = p;
+            ++np;
+        }
     }
+    long long r = 0, f = nrare;
+    for (long long k = 0; k < ntot; ++k) list[rare[k] ? r++ : f++] = items[k];
+    BatchLaunch L;
+    L.G = (const BatchGrid*)((char*)scratch + BL.off_grids);
+    L.ngrids = n;
+    L.step = (const int*)((char*)scratch + BL.off_step);
+    L.order = (const long long*)((char*)scratch + BL.off_order);
+    L.nitems = (int)ntot;
+    L.ctr = (unsigned long long*)((char*)scratch + BL.off_step + 64);
+    L.base0 = 0;
+    L.base_inc = counter_advance(ntot, slots);
+    L.probes = (const int*)((char*)scratch + BL.off_probes);
+    L.nprobes = np;
     int* dstep = (int*)((char*)scratch + BL.off_step);
-    const BatchGrid* dG = (const BatchGrid*)((char*)scratch + BL.off_grids);
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    if (rc == TF_OK && (cudaMemcpyAsync((char*)scratch + BL.off_grids, G, sizeof(BatchGrid) * (size_t)n,
-                                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
-                        cudaMemcpyAsync((char*)scratch + BL.off_amp, amp_host, BL.bytes - BL.off_amp,
-                                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
-                        cudaMemsetAsync(dstep, 0, sizeof(int), st) != cudaSuccess))
+    if (rc == TF_OK &&
+        (cudaMemcpyAsync((char*)scratch + BL.off_grids, G, sizeof(BatchGrid) * (size_t)n, cudaMemcpyHostToDevice, st) !=
+             cudaSuccess ||
+         cudaMemcpyAsync((char*)scratch + BL.off_probes, probes, sizeof(int) * 2 * (size_t)(np > 0 ? np : 1),
+                         cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync((char*)scratch + BL.off_order, list, sizeof(long long) * (size_t)(ntot > 0 ? ntot : 1),
+                         cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync((char*)scratch + BL.off_amp, amp_host, BL.bytes - BL.off_amp, cudaMemcpyHostToDevice, st) !=
+             cudaSuccess ||
+         cudaMemsetAsync((char*)scratch + BL.off_step, 0, kAlign, st) != cudaSuccess))
         rc = TF_ECUDA;
     // one launch per step over all grids, K steps captured in a CUDA graph and
     // replayed (the step number lives on the device; a one-thread launch
     // advances it after each step), the remaining steps launched directly
     const int64_t K = nsteps < kBatchGraphSteps ? nsteps : kBatchGraphSteps;
-    if (rc == TF_OK && nsteps >= K && K > 1) {
+    if (rc == TF_OK && K > 1) {
         cudaStream_t cs = nullptr;
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
             rc = TF_ECUDA;
         } else {
             cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             for (int64_t k = 0; k < K && e == cudaSuccess; ++k) {
-                e = launch_step_batch(dG, n, dstep, slots, cs);
+                e = launch_step_batch(L, slots, cs);
                 if (e == cudaSuccess) e = launch_step_advance(dstep, cs);
             }
             const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -1073,7 +1076,7 @@ tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, const double*
         for (; done + K <= nsteps; done += K)
             if (cudaGraphLaunch(exec, st) != cudaSuccess) { rc = TF_ECUDA; break; }
     for (; rc == TF_OK && done < nsteps; ++done)
-        if (launch_step_batch(dG, n, dstep, slots, st) != cudaSuccess || launch_step_advance(dstep, st) != cudaSuccess)
+        if (launch_step_batch(L, slots, st) != cudaSuccess || launch_step_advance(dstep, st) != cudaSuccess)
             rc = TF_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess && rc == TF_OK) rc = TF_ECUDA;
     if (exec) cudaGraphExecDestroy(exec);
@@ -1082,7 +1085,6 @@ tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, const double*
         for (int i = 0; i < n; ++i) {   // each handle holds the state the run reached
             tf_ctx* h = hs[i];
             h->level += nsteps;
-            h->O.base = G[i].base0 + (unsigned long long)nsteps * G[i].base_inc;
             if (nsteps & 1) {
                 const int t = h->cur;
                 h->cur = h->nxt;
@@ -1092,7 +1094,7 @@ tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, const double*
             bind(h, h->cur, h->nxt, h->P, h->O);
             h->O.base = base;
         }
-    free(w); free(cnt); free(G); free(amp_host);
+    free(G); free(amp_host); free(items); free(list); free(rare); free(probes);
     return rc;
 }
 

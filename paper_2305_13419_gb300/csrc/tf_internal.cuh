@@ -304,8 +304,8 @@ struct TMaps {
 };
 
 // Batched stepping (tf_batch_run): one launch of the single-step kernel per
-// step over every grid of a batch; each grid owns the CTAs [b0, b1) of the
-// launch.  Per grid, in global memory (written by the host before the run):
+// step over every grid of a batch.  Per grid, in global memory (written by
+// the host before the run):
 struct __align__(128) BatchGrid {
     TMaps tm;
     Params P[2];        // the step from the current buffer (index 0) and from the next one (index 1)
@@ -314,10 +314,24 @@ struct __align__(128) BatchGrid {
     Probes R;
     const float* amp;   // [step][source]: amp * s(t^{n+1}) of each step of the run
     long long level0;   // level at step 0 of the run
-    unsigned long long base0, base_inc;   // counter value at step 0, advance per step
-    int b0, b1;
 };
-cudaError_t launch_step_batch(const BatchGrid* grids, int ngrids, const int* step, int blocks, cudaStream_t st);
+// the launch: one work list over all grids (descriptor bits 48-62: the
+// grid's index), its counter, and the (grid, probe) pairs sampled per step
+struct BatchLaunch {
+    const BatchGrid* G;
+    int ngrids;
+    const int* step;                  // the step number (device), advanced after each launch
+    const long long* order;
+    int nitems;
+    unsigned long long* ctr;
+    unsigned long long base0, base_inc;   // counter value at step 0, advance per step
+    const int* probes;                // nprobes pairs (grid, probe)
+    int nprobes;
+};
+__host__ __device__ __forceinline__ long long item_with_grid(long long d, int grid) {
+    return d | (long long)grid << 48;
+}
+cudaError_t launch_step_batch(const BatchLaunch& BL, int blocks, cudaStream_t st);
 cudaError_t launch_step_advance(int* step, cudaStream_t st);
 
 // launchers (tf_kernels.cu)

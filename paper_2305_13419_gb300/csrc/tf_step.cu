@@ -261,29 +261,42 @@ __device__ __forceinline__ bool item_is_rare(const Params& P, const Sources& S, 
 
 }  // namespace
 
+// the arguments of the grid a work item belongs to
+struct GridRef {
+    const TMaps* tm;
+    const Params* P;
+    const StepOut* O;
+    const Sources* S;
+    const Probes* R;
+    const float* amp;   // batched: this grid's amplitude table ([step][source])
+    long long level;
+};
+
 // kBatch = false: one grid, its arguments by value.  kBatch = true: one step
-// of a batch of grids (tf_batch_run); the CTA works on the grid whose CTA
-// range holds it, with that grid's arguments from global memory and the step
-// number read from `step_ptr` (so that a captured launch can be replayed).
+// of a batch of grids (tf_batch_run): the work items of every grid form one
+// list (the grid's index in descriptor bits 48-62), each item runs with its
+// grid's arguments from global memory, and the step number is read from the
+// device (so that a captured launch can be replayed).
 template <bool kBatch>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_step_t(const __grid_constant__ TMaps tmk, Params Pk, StepOut Ok, Sources Sk, Probes Rk, long long levelk,
-             const BatchGrid* __restrict__ G, int ngrids, const int* __restrict__ step_ptr) {
-    int gi = 0;
-    if constexpr (kBatch)
-        while (gi + 1 < ngrids && (int)blockIdx.x >= G[gi + 1].b0) ++gi;
-    const BatchGrid* A = G + gi;
-    const int step = kBatch ? __ldg(step_ptr) : 0;
-    const TMaps& tm = kBatch ? A->tm : tmk;
-    const Params& P = kBatch ? A->P[step & 1] : Pk;
-    const StepOut& O = kBatch ? A->O[step & 1] : Ok;
-    const Sources& S = kBatch ? A->S : Sk;
-    const Probes& R = kBatch ? A->R : Rk;
-    const long long level = kBatch ? A->level0 + step : levelk;
-    const unsigned long long obase = kBatch ? A->base0 + (unsigned long long)step * A->base_inc : Ok.base;
-    const int bidx = kBatch ? (int)blockIdx.x - A->b0 : (int)blockIdx.x;
-    const int gdim = kBatch ? A->b1 - A->b0 : (int)gridDim.x;
-    auto amp_of = [&](int s) -> float { return kBatch ? __ldg(A->amp + (long long)step * S.n + s) : S.amp[s]; };
+    k_step_t(const __grid_constant__ TMaps tmk, const __grid_constant__ Params Pk, const __grid_constant__ StepOut Ok,
+             const __grid_constant__ Sources Sk, const __grid_constant__ Probes Rk, long long levelk,
+             const __grid_constant__ BatchLaunch BL) {
+    const int step = kBatch ? __ldg(BL.step) : 0;
+    const int par = step & 1;
+    auto gridref = [&](long long item) -> GridRef {
+        if constexpr (kBatch) {
+            const BatchGrid& A = BL.G[(unsigned long long)item >> 48];
+            return {&A.tm, &A.P[par], &A.O[par], &A.S, &A.R, A.amp, A.level0 + step};
+        } else {
+            return {&tmk, &Pk, &Ok, &Sk, &Rk, nullptr, levelk};
+        }
+    };
+    const long long* order = kBatch ? BL.order : Ok.order;
+    const int nitems = kBatch ? BL.nitems : Ok.nitems;
+    unsigned long long* const ctr = kBatch ? BL.ctr : Ok.ctr;
+    const unsigned long long obase = kBatch ? BL.base0 + (unsigned long long)step * BL.base_inc : Ok.base;
+    const int gdim = (int)gridDim.x;
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     // TMA destinations must be 128-byte aligned: round the base up (128 spare bytes are allocated)
     unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
@@ -299,23 +312,23 @@ __global__ void __launch_bounds__(kThreads, 2)
     // y0+15 and the item's planes
     __shared__ __align__(16) float s_cf[2][4][kCfN];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
-    const int nitems = O.nitems;
-    const int PL = (int)P.plane;
-    const bool mur = P.bc[2] == TF_BC_MUR;
 
     // Items 0 .. 2G - 1 (G CTAs) are handed out without the counter: CTA b
     // starts with items b and G + b.  The others come from the counter.
     // producer: a ticket from the counter, and later the work item it names
     // (or -1); the two halves are a plane apart, so that the counter's round
     // trip does not hold up the producer's warp
-    auto ticket = [&]() -> unsigned long long { return atomicAdd(O.ctr, 1ull); };
+    auto ticket = [&]() -> unsigned long long { return atomicAdd(ctr, 1ull); };
     auto item_of = [&](unsigned long long tk) -> long long {
         const long long d = (long long)(tk - obase) + 2LL * gdim;
-        return (d >= 0 && d < nitems) ? __ldg(O.order + d) : -1LL;
+        return (d >= 0 && d < nitems) ? __ldg(order + d) : -1LL;
     };
     // the records of an item: loaded by threads < nq - 1 ...
     auto rec_load = [&](long long item, float4& r, float& cf) {
         if (item < 0) return;
+        const GridRef g = gridref(item);
+        const Params& P = *g.P;
+        const StepOut& O = *g.O;
         const Tile t = tile_of(P, O, item);
         if (tid < t.nq - 1) r = __ldg(O.tilemat + (long long)(t.by * O.ntx + t.bx) * P.N[2] + plane_of(P, t, tid));
         // one coefficient table entry per thread: profile tid / kCfN, entry tid % kCfN
@@ -341,6 +354,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     auto rec_store = [&](long long item, int slot, const float4& r, float cf) {
         if (item < 0) return;
         (&s_cf[slot][0][0])[tid] = cf;
+        const GridRef g = gridref(item);
+        const Params& P = *g.P;
+        const StepOut& O = *g.O;
+        const Sources& S = *g.S;
+        const bool mur = P.bc[2] == TF_BC_MUR;
         const Tile t = tile_of(P, O, item);
         if (tid < t.nq - 1) {
             const int k = plane_of(P, t, tid);
@@ -371,8 +389,13 @@ __global__ void __launch_bounds__(kThreads, 2)
     int c_ord = 0;                                 // consumer: item ordinal
     Tile p_t;                                      // producer: tile of item p_ord
     p_t.nq = 0;
+    long long p_item = -1;                         // producer: item p_ord
     bool p_have = false;
     auto issue = [&](const Tile& t, int q, unsigned long long seq) {
+        const GridRef g = gridref(p_item);
+        const Params& P = *g.P;
+        const StepOut& O = *g.O;
+        const TMaps& tm = *g.tm;
         const int s = (int)(seq % kStages);
         const int k = plane_of(P, t, q);
         const int sax = slab_axis(slab_bits(P, t, k));
@@ -390,7 +413,9 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (!p_have) {
                 const long long item = s_item[p_ord & 1];
                 if (item < 0) return;
-                p_t = tile_of(P, O, item);
+                const GridRef g = gridref(item);
+                p_t = tile_of(*g.P, *g.O, item);
+                p_item = item;
                 p_have = true;
             }
             if (p_q >= p_t.nq) {
@@ -399,7 +424,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                 if (item < 0) return;
                 ++p_ord;
                 p_q = 0;
-                p_t = tile_of(P, O, item);
+                const GridRef g = gridref(item);
+                p_t = tile_of(*g.P, *g.O, item);
+                p_item = item;
             }
             issue(p_t, p_q, issued);
             ++p_q;
@@ -411,15 +438,18 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         if constexpr (kBatch) {
-            // the grid's tensor maps sit in global memory that the host rewrites
+            // the grids' tensor maps sit in global memory that the host rewrites
             // between runs: order those writes before the tensor-map proxy reads them
-            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(&tm.e) : "memory");
-            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(&tm.b) : "memory");
-            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(&tm.pb) : "memory");
+            for (int gi = 0; gi < BL.ngrids; ++gi) {
+                const TMaps* m = &BL.G[gi].tm;
+                asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(&m->e) : "memory");
+                asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(&m->b) : "memory");
+                asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(&m->pb) : "memory");
+            }
         }
-        const int b = bidx, g = gdim;
-        s_item[0] = b < nitems ? __ldg(O.order + b) : -1LL;
-        s_item[1] = (s_item[0] >= 0 && g + b < nitems) ? __ldg(O.order + g + b) : -1LL;
+        const int b = (int)blockIdx.x, g = gdim;
+        s_item[0] = b < nitems ? __ldg(order + b) : -1LL;
+        s_item[1] = (s_item[0] >= 0 && g + b < nitems) ? __ldg(order + g + b) : -1LL;
     }
     __syncthreads();
     {
@@ -434,7 +464,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     // while the ring fills: E^n at the probe points into their DFTs, a probe per CTA
     if (tid < TF_MAX_FREQS)
-        for (int pr = bidx; pr < R.n; pr += gdim) probe_update(P.E, R, pr, tid, level);
+        if constexpr (kBatch) {
+            for (int pr = blockIdx.x; pr < BL.nprobes; pr += gdim) {   // (grid, probe) pairs of the batch
+                const BatchGrid& A = BL.G[BL.probes[2 * pr]];
+                probe_update(A.P[par].E, A.R, BL.probes[2 * pr + 1], tid, A.level0 + step);
+            }
+        } else {
+            for (int pr = blockIdx.x; pr < Rk.n; pr += gdim) probe_update(Pk.E, Rk, pr, tid, levelk);
+        }
 
     int cur = 0;
     bool aborted = false;
@@ -443,9 +480,21 @@ __global__ void __launch_bounds__(kThreads, 2)
     long long pend = -1;           // producer: the item after the next one
     unsigned long long ptk = 0;    // producer: its ticket
     bool phas = false;             // producer: a ticket was drawn for it
+    unsigned* status = kBatch ? nullptr : Pk.status;   // the current item's grid's status word
     while (true) {
         const long long item = s_item[cur];
         if (item < 0) break;
+        const GridRef gr = gridref(item);
+        const Params& P = *gr.P;
+        const StepOut& O = *gr.O;
+        const Sources& S = *gr.S;
+        const int PL = (int)P.plane;
+        const bool mur = P.bc[2] == TF_BC_MUR;
+        status = P.status;
+        auto amp_of = [&](int s) -> float {
+            if constexpr (kBatch) return __ldg(gr.amp + (long long)step * S.n + s);
+            else return S.amp[s];
+        };
         const Tile t = tile_of(P, O, item);
         const int x0 = t.x0, y0 = t.y0, kz0 = t.kz0, nq = t.nq;
 
@@ -924,7 +973,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         // a copy never landed: flag it, give the copies in flight a bounded
         // time to finish (they write this CTA's shared memory), stop
         if (tid == kProd) {
-            atomicOr(P.status, kStatusTimeout);
+            if (status) atomicOr(status, kStatusTimeout);
             for (unsigned long long gi = consumed; gi < issued; ++gi)
                 mbar_wait(&bar[gi % kStages], (unsigned)((gi / kStages) & 1));
         }
@@ -1026,14 +1075,16 @@ cudaError_t launch_step(const void* tmaps, const Params& P, const StepOut& O, co
     static cudaError_t attr = step_smem_attribute();
     if (attr != cudaSuccess) return attr;
     const TMaps* tm = (const TMaps*)tmaps;
-    k_step_t<false><<<blocks, dim3(kTX, kThreadsY), step_smem_bytes(), st>>>(*tm, P, O, S, R, n, nullptr, 0, nullptr);
+    BatchLaunch none;
+    memset(&none, 0, sizeof(none));
+    k_step_t<false><<<blocks, dim3(kTX, kThreadsY), step_smem_bytes(), st>>>(*tm, P, O, S, R, n, none);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_batch(const BatchGrid* grids, int ngrids, const int* step, int blocks, cudaStream_t st) {
+cudaError_t launch_step_batch(const BatchLaunch& BL, int blocks, cudaStream_t st) {
     static cudaError_t attr = step_smem_attribute();
     if (attr != cudaSuccess) return attr;
-    // the by-value arguments are unused in a batched launch
+    // the by-value grid arguments are unused in a batched launch
     TMaps tm;
     memset(&tm, 0, sizeof(tm));
     Params P;
@@ -1044,7 +1095,7 @@ cudaError_t launch_step_batch(const BatchGrid* grids, int ngrids, const int* ste
     memset(&S, 0, sizeof(S));
     Probes R;
     memset(&R, 0, sizeof(R));
-    k_step_t<true><<<blocks, dim3(kTX, kThreadsY), step_smem_bytes(), st>>>(tm, P, O, S, R, 0, grids, ngrids, step);
+    k_step_t<true><<<blocks, dim3(kTX, kThreadsY), step_smem_bytes(), st>>>(tm, P, O, S, R, 0, BL);
     return cudaGetLastError();
 }
 

@@ -102,7 +102,7 @@ def load(build_if_missing: bool = True):
                        ("tf_adjoint_run", [vp, C.c_int64, C.c_int, C.c_int, C.c_int, vp, C.c_size_t, dp, vp, vp]),
                        ("tf_batch_step", [C.POINTER(vp), C.c_int, C.c_int64]),
                        ("tf_batch_scratch_size", [C.POINTER(vp), C.c_int, C.c_int64, C.POINTER(C.c_size_t)]),
-                       ("tf_batch_run", [C.POINTER(vp), C.c_int, C.c_int64, dp, vp, C.c_size_t]),
+                       ("tf_batch_run", [C.POINTER(vp), C.c_int, C.c_int64, vp, C.c_size_t]),
                        ("tf64_create", [C.POINTER(tf_grid_desc), vp, C.c_size_t, C.POINTER(vp)]),
                        ("tf64_destroy", [vp]), ("tf64_set_materials", [vp, vp, vp, vp, vp]),
                        ("tf64_set_field", [vp, C.c_int, vp]),
@@ -319,11 +319,10 @@ def batch_step(grids, nsteps: int):
     _check(load().tf_batch_step(hs, len(grids), int(nsteps)), "tf_batch_step")
 
 
-def batch_run(grids, nsteps: int, weights=None):
+def batch_run(grids, nsteps: int):
     """Advance every grid of `grids` by nsteps with one launch per step over
-    all of them (tf_batch_run), the steps replayed from a CUDA graph; CTAs
-    are split among the grids by `weights` (e.g. measured ms per step) or by
-    cells with CPML cells counted 2.5 times.  Synchronises."""
+    all of them (tf_batch_run): one work list over all grids' items, the
+    steps replayed from a CUDA graph.  Synchronises."""
     import torch
     hs = (C.c_void_p * len(grids))(*[g.h for g in grids])
     n = C.c_size_t()
@@ -331,12 +330,7 @@ def batch_run(grids, nsteps: int, weights=None):
     scratch = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=grids[0].device)
     base = int(scratch.data_ptr())
     off = (-base) % 256
-    wp = None
-    if weights is not None:
-        wa = np.ascontiguousarray(np.asarray(weights, np.float64))
-        wp = wa.ctypes.data_as(C.POINTER(C.c_double))
-    _check(load().tf_batch_run(hs, len(grids), int(nsteps), wp, C.c_void_p(base + off), int(n.value)),
-           "tf_batch_run")
+    _check(load().tf_batch_run(hs, len(grids), int(nsteps), C.c_void_p(base + off), int(n.value)), "tf_batch_run")
     del scratch
 
 
