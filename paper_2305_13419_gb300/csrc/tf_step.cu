@@ -261,6 +261,21 @@ __device__ __forceinline__ bool item_is_rare(const Params& P, const Sources& S, 
 
 }  // namespace
 
+// batched launches: the arguments of a work item's grid as the plane loop
+// reads them, staged in shared memory
+struct ItemArgs {
+    Params P;
+    StepOut O;
+    Sources S;
+    const float* amp;
+};
+// copy `n` bytes (a multiple of 4) with every thread of the CTA
+__device__ __forceinline__ void cta_copy(void* dst, const void* src, int n, int tid, int nth) {
+    const unsigned* s = reinterpret_cast<const unsigned*>(src);
+    unsigned* d = reinterpret_cast<unsigned*>(dst);
+    for (int i = tid; i < n / 4; i += nth) d[i] = __ldg(s + i);
+}
+
 // the arguments of the grid a work item belongs to
 struct GridRef {
     const TMaps* tm;
@@ -311,7 +326,22 @@ __global__ void __launch_bounds__(kThreads, 2)
     // (b_B, c_B, b_E, c_E) the tile's columns x0-4 .. x0+31, rows y0-1 ..
     // y0+15 and the item's planes
     __shared__ __align__(16) float s_cf[2][4][kCfN];
+    // batched: the grid arguments of the current and the next item (slot as s_item)
+    __shared__ __align__(16) unsigned char s_args_raw[kBatch ? 2 * sizeof(ItemArgs) : 16];
+    ItemArgs* s_args = reinterpret_cast<ItemArgs*>(s_args_raw);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
+    // stage the grid arguments of `item` in slot `slot` (every thread; visible after the next barrier)
+    auto stage_args = [&](long long item, int slot) {
+        if constexpr (kBatch) {
+            if (item < 0) return;
+            const BatchGrid& A = BL.G[(unsigned long long)item >> 48];
+            ItemArgs& D = s_args[slot];
+            cta_copy(&D.P, &A.P[par], (int)sizeof(Params), tid, kThreads);
+            cta_copy(&D.O, &A.O[par], (int)sizeof(StepOut), tid, kThreads);
+            cta_copy(&D.S, &A.S, (int)sizeof(Sources), tid, kThreads);
+            if (tid == 0) D.amp = A.amp;
+        }
+    };
 
     // Items 0 .. 2G - 1 (G CTAs) are handed out without the counter: CTA b
     // starts with items b and G + b.  The others come from the counter.
@@ -459,6 +489,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         rec_load(s_item[1], r1, f1);
         rec_store(s_item[0], 0, r0, f0);
         rec_store(s_item[1], 1, r1, f1);
+        stage_args(s_item[0], 0);
+        stage_args(s_item[1], 1);
     }
     if (tid == kProd) pump();
     __syncthreads();
@@ -484,15 +516,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     while (true) {
         const long long item = s_item[cur];
         if (item < 0) break;
-        const GridRef gr = gridref(item);
-        const Params& P = *gr.P;
-        const StepOut& O = *gr.O;
-        const Sources& S = *gr.S;
+        const ItemArgs& IA = s_args[cur];
+        const Params& P = kBatch ? IA.P : Pk;
+        const StepOut& O = kBatch ? IA.O : Ok;
+        const Sources& S = kBatch ? IA.S : Sk;
         const int PL = (int)P.plane;
         const bool mur = P.bc[2] == TF_BC_MUR;
         status = P.status;
         auto amp_of = [&](int s) -> float {
-            if constexpr (kBatch) return __ldg(gr.amp + (long long)step * S.n + s);
+            if constexpr (kBatch) return __ldg(IA.amp + (long long)step * S.n + s);
             else return S.amp[s];
         };
         const Tile t = tile_of(P, O, item);
@@ -766,7 +798,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                 }
                 if (qq == 1 || nq == 2) pend = phas ? item_of(ptk) : -1LL;
             }
-            if (qq == 0) rec_load(s_item[cur ^ 1], rnext, cfnext);
+            if (qq == 0) {
+                rec_load(s_item[cur ^ 1], rnext, cfnext);
+                stage_args(s_item[cur ^ 1], cur ^ 1);   // read from the next item on, after a barrier
+            }
 
             // ------------------------------------------------ E phase
             if (own) {
