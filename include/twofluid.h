@@ -199,6 +199,16 @@ tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t*
 tf_status tf_set_two_step(tf_handle h, int planes);
 tf_status tf_two_step_box(tf_handle h, int lo[3], int hi[3], int* active);
 
+/* The stepping kernels wait on an mbarrier for every plane they stage; each
+ * wait polls it at most `polls` times (default 2^22, far beyond a copy's
+ * latency).  A wait that runs out latches TF_ETIMEOUT for tf_sync(): the
+ * CTA then waits (with the default limit) for the copies it has in flight
+ * and returns, leaving the grid's fields undefined (the context stays
+ * usable; reload a checkpoint or rebuild the grid).  polls < 0 restores the
+ * default; polls = 0 makes every wait give up at once (a test of the error
+ * path).  Applies to the handle's later launches, batched ones included. */
+tf_status tf_set_wait_limit(tf_handle h, int64_t polls);
+
 /* Advance n independent grids by nsteps steps each (the batched workload:
  * many resonator variants at once).  The grids advance together, one step
  * of every grid in turn; each grid's work goes to its own handle's stream,

@@ -422,6 +422,7 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
     h->two_step_on = 1;
     h->tb_len = kTBLenMax;
     P.status = h->status;
+    P.wait_polls = kSpinLimit;
     {
         int dev = 0, sms = 1;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -849,6 +850,12 @@ tf_status tf_set_two_step(tf_handle h, int planes) {
         h->tb_len = planes;
         h->order_dirty = 1;   // the box's work list is cut again
     }
+    return TF_OK;
+}
+
+tf_status tf_set_wait_limit(tf_handle h, int64_t polls) {
+    if (!h) return TF_EINVAL;
+    h->P.wait_polls = polls < 0 ? kSpinLimit : (long long)polls;
     return TF_OK;
 }
 

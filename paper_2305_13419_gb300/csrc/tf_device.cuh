@@ -22,9 +22,10 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-// bounded wait for phase `phase` of a barrier; false if it never completed
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase) {
-    for (long long it = 0; it < kSpinLimit; ++it) {
+// bounded wait for phase `phase` of a barrier: at most `polls` polls, false
+// if the phase has not completed by then
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase, long long polls = kSpinLimit) {
+    for (long long it = 0; it < polls; ++it) {
         unsigned done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

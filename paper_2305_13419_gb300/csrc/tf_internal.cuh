@@ -63,6 +63,7 @@ struct Params {
     const float* pbB[3]; // ... at half-integer positions
     const float* pcB[3];
     unsigned* status;
+    long long wait_polls;  // polls of an mbarrier before a staged plane counts as lost
 };
 
 // Fused step (tf_step.cu): E, B, Js and psi_B live in three buffers (the

@@ -695,8 +695,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                     }
                 }
             }
-            bool ok = mbar_wait(&bar[g1 % kStages], (unsigned)((g1 / kStages) & 1));
-            if (qq == 0) ok = ok && mbar_wait(&bar[g0 % kStages], (unsigned)((g0 / kStages) & 1));
+            bool ok = mbar_wait(&bar[g1 % kStages], (unsigned)((g1 / kStages) & 1), P.wait_polls);
+            if (qq == 0) ok = ok && mbar_wait(&bar[g0 % kStages], (unsigned)((g0 / kStages) & 1), P.wait_polls);
             if (seam) {
                 if (qq == 0) patch(s0, k, sax);
                 const int k1 = plane_of(P, t, qq + 1);
@@ -1008,7 +1008,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         // a copy never landed: flag it, give the copies in flight a bounded
         // time to finish (they write this CTA's shared memory), stop
         if (tid == kProd) {
-            if (status) atomicOr(status, kStatusTimeout);
+            if constexpr (kBatch) {   // the CTA's later items, of any grid, stay undone
+                for (int gi = 0; gi < BL.ngrids; ++gi) atomicOr(BL.G[gi].P[par].status, kStatusTimeout);
+            } else {
+                if (status) atomicOr(status, kStatusTimeout);
+            }
             for (unsigned long long gi = consumed; gi < issued; ++gi)
                 mbar_wait(&bar[gi % kStages], (unsigned)((gi / kStages) & 1));
         }

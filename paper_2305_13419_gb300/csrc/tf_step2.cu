@@ -349,8 +349,8 @@ __global__ void __launch_bounds__(kThr, 2)
             const Stage2& s1 = stg[g1 % kStages];
             bool ok = true;
             if (doB1) {
-                ok = mbar_wait(&bar[g1 % kStages], (unsigned)((g1 / kStages) & 1));
-                if (it == 0) ok = ok && mbar_wait(&bar[g0 % kStages], (unsigned)((g0 / kStages) & 1));
+                ok = mbar_wait(&bar[g1 % kStages], (unsigned)((g1 / kStages) & 1), P.wait_polls);
+                if (it == 0) ok = ok && mbar_wait(&bar[g0 % kStages], (unsigned)((g0 / kStages) & 1), P.wait_polls);
             }
             // ------------------------------------------------ phase X
             if (ok && doB1) {
