@@ -421,11 +421,21 @@ __global__ void __launch_bounds__(kThreads, 2)
     p_t.nq = 0;
     long long p_item = -1;                         // producer: item p_ord
     bool p_have = false;
+    // the arguments the producer reads for item ordinal `ord`: batched, the
+    // staged copy of its slot (usable once a barrier has passed since the
+    // copy), else the launch's own
+    auto prod_P = [&](int ord) -> const Params& {
+        if constexpr (kBatch) return s_args[ord & 1].P;
+        else return Pk;
+    };
+    auto prod_O = [&](int ord) -> const StepOut& {
+        if constexpr (kBatch) return s_args[ord & 1].O;
+        else return Ok;
+    };
     auto issue = [&](const Tile& t, int q, unsigned long long seq) {
-        const GridRef g = gridref(p_item);
-        const Params& P = *g.P;
-        const StepOut& O = *g.O;
-        const TMaps& tm = *g.tm;
+        const Params& P = prod_P(p_ord);
+        const StepOut& O = prod_O(p_ord);
+        const TMaps& tm = kBatch ? BL.G[(unsigned long long)p_item >> 48].tm : tmk;
         const int s = (int)(seq % kStages);
         const int k = plane_of(P, t, q);
         const int sax = slab_axis(slab_bits(P, t, k));
@@ -438,24 +448,26 @@ __global__ void __launch_bounds__(kThreads, 2)
             tma_load_box(&stg[s].pb[0][0][0], &tm.pb, t.x0 - 4, t.y0 - 1, k,
                          kPsiGroup * O.psi_slot[sax] + O.psib_cur, &bar[s]);
     };
-    auto pump = [&]() {   // keep kStages planes in flight, crossing into the next item
+    // keep kStages planes in flight, crossing into the next item; batched,
+    // the item after the consumer's only once its staged arguments are
+    // visible (`next_visible`: a barrier has passed since they were copied)
+    auto pump = [&](bool next_visible) {
         while (issued < consumed + kStages) {
             if (!p_have) {
                 const long long item = s_item[p_ord & 1];
                 if (item < 0) return;
-                const GridRef g = gridref(item);
-                p_t = tile_of(*g.P, *g.O, item);
+                p_t = tile_of(prod_P(p_ord), prod_O(p_ord), item);
                 p_item = item;
                 p_have = true;
             }
             if (p_q >= p_t.nq) {
                 if (p_ord > c_ord) return;   // the next slot still holds the current item
+                if (kBatch && p_ord == c_ord && !next_visible) return;
                 const long long item = s_item[(p_ord + 1) & 1];
                 if (item < 0) return;
                 ++p_ord;
                 p_q = 0;
-                const GridRef g = gridref(item);
-                p_t = tile_of(*g.P, *g.O, item);
+                p_t = tile_of(prod_P(p_ord), prod_O(p_ord), item);
                 p_item = item;
             }
             issue(p_t, p_q, issued);
@@ -492,7 +504,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         stage_args(s_item[0], 0);
         stage_args(s_item[1], 1);
     }
-    if (tid == kProd) pump();
+    if constexpr (kBatch) __syncthreads();   // the staged arguments, for the producer
+    if (tid == kProd) pump(true);
     __syncthreads();
     // while the ring fills: E^n at the probe points into their DFTs, a probe per CTA
     if (tid < TF_MAX_FREQS)
@@ -516,6 +529,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     while (true) {
         const long long item = s_item[cur];
         if (item < 0) break;
+        // batched: planes of this item that the producer could not issue
+        // before its arguments were visible (items shorter than the ring)
+        if (kBatch && tid == kProd) pump(false);
         const ItemArgs& IA = s_args[cur];
         const Params& P = kBatch ? IA.P : Pk;
         const StepOut& O = kBatch ? IA.O : Ok;
@@ -791,7 +807,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (__syncthreads_or(!ok)) return false;
             if (tid == kProd) {
                 consumed = g0;
-                pump();
+                pump(qq >= 1);   // the next item's arguments were staged during plane 0
                 if (qq == 0) {
                     phas = s_item[cur ^ 1] >= 0;
                     if (phas) ptk = ticket();
