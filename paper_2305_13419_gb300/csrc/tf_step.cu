@@ -432,6 +432,9 @@ __global__ void __launch_bounds__(kThreads, 2)
         if constexpr (kBatch) return s_args[ord & 1].O;
         else return Ok;
     };
+    // stages that threads wrote with ordinary stores (periodic seam patches):
+    // a proxy fence orders those writes before the stage's next TMA copy
+    unsigned p_dirty = 0;
     auto issue = [&](const Tile& t, int q, unsigned long long seq) {
         const Params& P = prod_P(p_ord);
         const StepOut& O = prod_O(p_ord);
@@ -440,7 +443,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int k = plane_of(P, t, q);
         const int sax = slab_axis(slab_bits(P, t, k));
         const unsigned bytes = kEBytes + kBBytes + (sax >= 0 ? kPBBytes : 0u);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if ((p_dirty >> s) & 1u) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            p_dirty &= ~(1u << s);
+        }
         mbar_expect_tx(&bar[s], bytes);
         tma_load_box(&stg[s].e[0][0][0], &tm.e, t.x0 - 4, t.y0 - 1, k, O.ecur, &bar[s]);
         tma_load_box(&stg[s].b[0][0][0], &tm.b, t.x0 - 4, t.y0 - 1, k, O.bcur, &bar[s]);
@@ -717,6 +723,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 if (qq == 0) patch(s0, k, sax);
                 const int k1 = plane_of(P, t, qq + 1);
                 patch(s1, k1, slab_axis(slab_bits(P, t, k1)));
+                if (tid == kProd) p_dirty |= (qq == 0 ? 1u << (g0 % kStages) : 0u) | 1u << (g1 % kStages);
                 __syncthreads();
             }
 

@@ -258,7 +258,8 @@ __global__ void __launch_bounds__(kThr, 2)
     auto issue = [&](const It2& t, int q, unsigned long long seq) {
         const int s = (int)(seq % kStages);
         const int k = t.kz0 - 2 + q;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // no proxy fence: only TMA writes the stages, threads only read them,
+        // and the barrier before every issue orders those reads first
         mbar_expect_tx(&bar[s], kE2Bytes + kB2Bytes);
         tma_load_box(&stg[s].e[0][0][0], &tm.e, t.x0 - 4, t.y0 - 2, k, O.ecur, &bar[s]);
         tma_load_box(&stg[s].b[0][0][0], &tm.b, t.x0 - 4, t.y0 - 2, k, O.bcur, &bar[s]);
