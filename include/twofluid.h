@@ -281,11 +281,14 @@ tf_status tf_checkpoint_load(tf_handle h, const void* src, size_t bytes, int on_
  *   forward, saving a checkpoint every `segment` steps into the scratch,
  *   then walks the segments backwards: each is recomputed from its
  *   checkpoint with E kept at every level, and the transposed step runs back
- *   through it, summing per-edge gradients in FP64.  The adjoint's seed is
+ *   through it, summing per-edge gradients in FP64.  The recompute of the
+ *   segment before runs on a second stream of the library's (created and
+ *   destroyed by the call) beside those transposed steps, into the other of
+ *   two history buffers.  The adjoint's seed is
  *   scaled by a power of two to O(1) (and the gradients scaled back), so the
  *   FP32 adjoint state stays in FP32's normal range for any source size.
  *   scratch   caller-owned device memory of at least tf_adjoint_scratch_size
- *             bytes (checkpoints, one segment of E history, the adjoint
+ *             bytes (checkpoints, two segments of E history, the adjoint
  *             state, the gradient sums); TF_ENOMEM if smaller;
  *   J         host double: the objective;
  *   grad_eps, grad_lambda  device float arrays [nz][ny][nx] (cells):

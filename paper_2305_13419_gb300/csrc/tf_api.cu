@@ -1379,11 +1379,60 @@ AdjLayout adj_layout(const tf_ctx* h, int64_t nsteps, int segment) {
     A.nck = (size_t)A.nseg + 1;
     size_t o = 0;
     A.off_ck = o;    o += A.nck * A.ck;
-    A.off_hist = o;  o += (size_t)(segment + 1) * 3 * fb;
+    A.off_hist = o;  o += 2 * (size_t)(segment + 1) * 3 * fb;   // two segments' E history
     A.off_state = o; o += (size_t)(9 + 4 * h->L.ncpml_axes + 12) * fb;   // E, B, J, psi, edge and face weights
     A.off_grad = o;  o += 6 * align_up(sizeof(double) * (size_t)h->L.total);
     A.bytes = o;
     return A;
+}
+
+// the adjoint's second stream (higher priority: the recompute's CTAs are
+// placed as soon as an SM has room) and its events; released on every exit
+struct AdjStreams {
+    cudaStream_t rs = nullptr;
+    cudaEvent_t evR[2] = {nullptr, nullptr}, evA[2] = {nullptr, nullptr};
+    int sms = 1;
+    bool create() {
+        int dev = 0, lo = 0, hi = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            return false;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) return false;
+        if (cudaStreamCreateWithPriority(&rs, cudaStreamNonBlocking, hi) != cudaSuccess) return false;
+        for (int b = 0; b < 2; ++b)
+            if (cudaEventCreateWithFlags(&evR[b], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&evA[b], cudaEventDisableTiming) != cudaSuccess)
+                return false;
+        return true;
+    }
+    ~AdjStreams() {
+        if (rs) cudaStreamSynchronize(rs);
+        for (int b = 0; b < 2; ++b) {
+            if (evR[b]) cudaEventDestroy(evR[b]);
+            if (evA[b]) cudaEventDestroy(evA[b]);
+        }
+        if (rs) cudaStreamDestroy(rs);
+    }
+};
+
+// a checkpoint this run wrote (so its header needs no check) back into the
+// grid, enqueued on the handle's stream without waiting for it
+tf_status ckpt_restore_async(tf_ctx* h, const char* src, int64_t level, int primed) {
+    CkptPart parts[40];
+    const int n = ckpt_parts(h, parts);
+    size_t o = kCkptHeader;
+    for (int k = 0; k < n; ++k) {
+        TF_CUDA(cudaMemcpyAsync(parts[k].cur, src + o, parts[k].bytes, cudaMemcpyDeviceToDevice, h->stream));
+        for (int b = 0; b < 2; ++b)
+            if (parts[k].other[b])
+                TF_CUDA(cudaMemcpyAsync(parts[k].other[b], src + o, parts[k].bytes, cudaMemcpyDeviceToDevice,
+                                        h->stream));
+        o += parts[k].bytes;
+    }
+    TF_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream));
+    h->level = level;
+    h->primed = primed;
+    return TF_OK;
 }
 
 }  // namespace
@@ -1407,6 +1456,7 @@ tf_status tf_adjoint_run(tf_handle h, int64_t nsteps, int probe, int freq_index,
     const size_t gb = align_up(sizeof(double) * (size_t)h->L.total);
     tf_status rc;
     // forward run, a checkpoint at the start of every segment and at the end
+    // (every segment but the first starts primed)
     for (int64_t s = 0; s < A.nseg; ++s) {
         if ((rc = tf_checkpoint_save(h, sc + A.off_ck + s * A.ck, A.ck, 1)) != TF_OK) return rc;
         const int64_t len = (s + 1) * segment <= nsteps ? segment : nsteps - s * segment;
@@ -1464,23 +1514,52 @@ tf_status tf_adjoint_run(tf_handle h, int64_t nsteps, int probe, int freq_index,
     Sources src;
     fill_sources(h, src);
     const int64_t n0 = h->R.n0[probe];
-    auto hist = [&](int64_t m, int c) { return (float*)(sc + A.off_hist + ((size_t)m * 3 + c) * fb); };
-    for (int64_t s = A.nseg - 1; s >= 0; --s) {
-        // recompute the segment, keeping E at every level
-        if ((rc = tf_checkpoint_load(h, sc + A.off_ck + s * A.ck, A.ck, 1)) != TF_OK) return rc;
-        const int64_t len = (s + 1) * segment <= nsteps ? segment : nsteps - s * segment;
-        for (int64_t m = 0; m <= len; ++m) {
-            float* const dst[3] = {hist(m, 0), hist(m, 1), hist(m, 2)};
-            TF_CUDA(launch_copy3(dst, h->P.E, h->L.total, h->stream));
-            if (m < len && (rc = tf_step(h, 1)) != TF_OK) return rc;
+    // E history of segment s in buffer s % 2
+    auto hist = [&](int64_t s, int64_t m, int c) {
+        return (float*)(sc + A.off_hist + (((size_t)(s & 1) * (segment + 1) + m) * 3 + c) * fb);
+    };
+    auto seg_len = [&](int64_t s) { return (s + 1) * segment <= nsteps ? segment : nsteps - s * segment; };
+    // The recompute of segment s - 1 (forward steps from its checkpoint,
+    // keeping E at every level) runs on a second stream, beside the adjoint
+    // steps of segment s on the handle's stream: the two touch different
+    // memory (the grid's fields / the adjoint state; each its own history
+    // buffer).  The recompute's step kernel takes one CTA per SM, leaving
+    // the rest of each SM to the adjoint passes.
+    AdjStreams X;
+    if (!X.create()) return TF_ECUDA;
+    cudaStream_t const user = h->stream;
+    const int keep_blocks = h->step_blocks;
+    auto recompute = [&](int64_t s) -> tf_status {
+        h->stream = X.rs;
+        h->step_blocks = keep_blocks < X.sms ? keep_blocks : X.sms;
+        tf_status r = ckpt_restore_async(h, sc + A.off_ck + s * A.ck, s * segment, s > 0 ? 1 : 0);
+        const int64_t len = seg_len(s);
+        for (int64_t m = 0; r == TF_OK && m <= len; ++m) {
+            float* const dst[3] = {hist(s, m, 0), hist(s, m, 1), hist(s, m, 2)};
+            if (launch_copy3(dst, h->P.E, h->L.total, h->stream) != cudaSuccess) r = TF_ECUDA;
+            else if (m < len) r = tf_step(h, 1);
         }
+        if (r == TF_OK && cudaEventRecord(X.evR[s & 1], X.rs) != cudaSuccess) r = TF_ECUDA;
+        h->stream = user;
+        h->step_blocks = keep_blocks;
+        return r;
+    };
+    if ((rc = recompute(A.nseg - 1)) != TF_OK) return rc;
+    for (int64_t s = A.nseg - 1; s >= 0; --s) {
+        // this segment's history is complete
+        TF_CUDA(cudaStreamWaitEvent(user, X.evR[s & 1], 0));
+        if (s > 0) {   // the previous segment's recompute into the other buffer, once its last reader is done
+            if (s + 1 < A.nseg) TF_CUDA(cudaStreamWaitEvent(X.rs, X.evA[(s + 1) & 1], 0));
+            if ((rc = recompute(s - 1)) != TF_OK) return rc;
+        }
+        const int64_t len = seg_len(s);
         // adjoint steps back through the segment
         for (int64_t m = len - 1; m >= 0; --m) {
             const int64_t n = s * segment + m;
             AdjStep st;
             for (int c = 0; c < 3; ++c) {
-                st.En[c] = hist(m, c);
-                st.En1[c] = hist(m + 1, c);
+                st.En[c] = hist(s, m, c);
+                st.En1[c] = hist(s, m + 1, c);
             }
             st.probe_comp = h->R.comp[probe];
             st.probe_q = h->R.q[probe];
@@ -1495,7 +1574,9 @@ tf_status tf_adjoint_run(tf_handle h, int64_t nsteps, int probe, int freq_index,
             for (int q = 0; q < h->nsrc; ++q) src.amp[q] = (float)(h->src[q].amp * waveform(h->src[q], t1));
             TF_CUDA(launch_adjoint_step(h->P, S, src, st, h->O.tilemat, h->L.ntx, h->stream));
         }
+        TF_CUDA(cudaEventRecord(X.evA[s & 1], user));
     }
+    TF_CUDA(cudaStreamWaitEvent(user, X.evR[0], 0));   // the last recompute (segment 0)
     TF_CUDA(launch_adjoint_cells(h->P, S, (float)(kC0 * h->dt), 1.0 / seed_scale, grad_eps, grad_lambda,
                                  h->stream));
     // leave the handle in the state the forward run reached
