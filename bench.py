@@ -226,9 +226,10 @@ def algorithmic_bytes(w, N, box=None):
 
 
 def source_hash():
-    """Hash of the sources that define the step kernel (its file and the shared header)."""
+    """Hash of the sources that define the step kernels (single-step and
+    two-step kernels, their shared headers)."""
     h = hashlib.sha256()
-    for f in ("tf_step.cu", "tf_internal.cuh"):
+    for f in ("tf_step.cu", "tf_step2.cu", "tf_internal.cuh", "tf_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2305_13419_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -330,13 +331,14 @@ def config_block(state_bytes=None):
     return c
 
 
-def roofline_of(w, g, kt):
+def roofline_of(w, g, kt, planes=16):
     """Roofline of the step kernels from their algorithmic bytes per launch
     over their mean event-timed launch durations, against the measured HBM
     peak.  With two-step passes the two-step kernel (the interior box, two
     steps per launch) and the single-step kernel (the rest of the grid, one
     step per launch) are listed apart; the dominant one (larger share of the
-    run's kernel time) heads the object."""
+    run's kernel time) heads the object.  `planes`: the two-step work-item
+    length the run used (the ncu traffic is keyed by it)."""
     peak, peak_kind = hbm_peak()
     (lo, hi), active = g.two_step_box()
     two = "step2" in kt
@@ -350,11 +352,13 @@ def roofline_of(w, g, kt):
     else:
         kernels["k_step"] = {"algorithmic_bytes": ab["step"], "points": ab["points"], "steps_per_launch": 1,
                              "ms": kt["step"][0], "launches": kt["step"][1]}
+    # ncu traffic keys: the launch kind on the workload
+    keys = {"k_step2": f"{w.name}/two-step-{planes}", "k_step": f"{w.name}/shell" if two else w.name}
     for k, v in kernels.items():
         v["achieved_GBps"] = v["algorithmic_bytes"] / (v["ms"] * 1e-3) / 1e9
         v["frac"] = v["achieved_GBps"] / peak
         v["share"] = v["ms"] * v["launches"]
-        v["traffic"] = ncu_traffic(k, w.name)
+        v["traffic"] = ncu_traffic(k, keys[k])
     tot = sum(v["share"] for v in kernels.values())
     for v in kernels.values():
         v["share"] /= tot
@@ -408,7 +412,7 @@ def run_ours(args, ws, rank, local):
     g.sync()
     ms_max = max_over_ranks(dist, ms, dev)
     value = aggregate(w.ncells, args.steps, ms_max, ws)
-    ab, roof = roofline_of(w, g, kt)
+    ab, roof = roofline_of(w, g, kt, planes=tuning["best"] if tuning and tuning["best"] else 16)
     state_bytes = (9 + 3) * 4 * ab["points"]
     launches = sum(v[1] for v in kt.values())
     g.close()
@@ -503,6 +507,8 @@ def run_batch(args, plain_gcells):
     cells = sum(w.ncells for w in ws)
     out = {"grids": len(ws), "cells": cells, "steps": args.batch_steps, "sizes": [96, 128, 160]}
     grids = [tf.Grid.from_workload(w) for w in ws]
+    # algorithmic bytes of one batched launch: every grid's one-pass bytes
+    ab = sum(algorithmic_bytes(w, g.N)["step"] for w, g in zip(ws, grids))
     tf.batch_run(grids, 10)
     torch.cuda.synchronize()
     st = grids[0].stream
@@ -517,10 +523,17 @@ def run_batch(args, plain_gcells):
         gg.close()
     del grids
     torch.cuda.empty_cache()
-    out["one_launch"] = {"ms_per_step": ms / args.batch_steps,
+    peak, peak_kind = hbm_peak()
+    mps = ms / args.batch_steps
+    out["one_launch"] = {"ms_per_step": mps,
                          "gcell_updates_per_s": cells * args.batch_steps / (ms * 1e-3) / 1e9,
                          "timing": "CUDA events on the batch's stream around tf_batch_run (includes its set-up "
-                                   "uploads and graph capture)"}
+                                   "uploads and graph capture)",
+                         "roofline": {"bound": "hbm", "kernel": "k_step_t<batch>", "algorithmic_bytes": ab,
+                                      "achieved": ab / (mps * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                                      "frac": ab / (mps * 1e-3) / 1e9 / peak,
+                                      "traffic": ncu_traffic("k_step_batch", "batch-64-cpw"),
+                                      "peak_source": peak_kind}}
     streams = [torch.cuda.Stream() for _ in range(8)]
     grids = [tf.Grid.from_workload(w, stream=streams[i % 8]) for i, w in enumerate(ws)]
     tf.batch_step(grids, 10)
@@ -570,6 +583,46 @@ def run_batch_singles(args):
     return 0
 
 
+def run_batch_overhead(args):
+    """The batched kernel against the single-grid kernel on the same grid:
+    tf_batch_run of a one-grid list and tf_step (single steps), each timed
+    with CUDA events on the grid's stream, on the 512 x 256 x 128 and
+    1024 x 512 x 256 CPWs.  One JSON line."""
+    import torch
+    from paper_2305_13419_gb300 import twofluid as tf
+    from paper_2305_13419_gb300 import workloads as W
+    rows = []
+    for w in (W.cpw(), W.cpw_large()):
+        g = tf.Grid.from_workload(w)
+        g.set_two_step(0)
+        g.step(6)
+        g.sync()
+        st = g.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 256
+        e0.record(st)
+        g.step(n)
+        e1.record(st)
+        torch.cuda.synchronize()
+        single = e0.elapsed_time(e1) / n
+        tf.batch_run([g], 66)
+        torch.cuda.synchronize()
+        e0.record(st)
+        tf.batch_run([g], n)
+        e1.record(st)
+        torch.cuda.synchronize()
+        batched = e0.elapsed_time(e1) / n
+        g.sync()
+        rows.append({"grid": w.name, "single_grid_kernel_ms_per_step": single, "batched_kernel_ms_per_step": batched,
+                     "ratio": batched / single})
+        g.close()
+        del g
+        torch.cuda.empty_cache()
+    print(json.dumps({"measure": "batched kernel on one grid vs the single-grid kernel", "steps": 256,
+                      "grids": rows}), flush=True)
+    return 0
+
+
 def run_config(w, steps, warmup=5, two_step=True, autotune_steps=0):
     """GPU throughput of the plain step on one workload: the whole run and
     the step kernel's own launches timed with CUDA events on the handle's
@@ -589,7 +642,7 @@ def run_config(w, steps, warmup=5, two_step=True, autotune_steps=0):
     torch.cuda.synchronize()
     kt, ms = g.step_timed(steps, with_total=True)
     g.sync()
-    _, roof = roofline_of(w, g, kt)
+    _, roof = roofline_of(w, g, kt, planes=tuning["best"] if tuning and tuning["best"] else 16)
     g.close()
     del g
     torch.cuda.empty_cache()
@@ -766,6 +819,8 @@ def main(argv=None):
     ap.add_argument("--fp64-peak", action="store_true", help="measure only the FP64 FMA rate (one JSON line)")
     ap.add_argument("--batch-singles", type=int, default=0,
                     help="time only the first N grids of the batch one at a time (one JSON line)")
+    ap.add_argument("--batch-overhead", action="store_true",
+                    help="only the batched kernel against the single-grid kernel on one grid (one JSON line)")
     ap.add_argument("--study-workload", choices=("cpw", "cpw_large"), default="cpw")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--adjoint-steps", type=int, default=8000)
@@ -780,6 +835,8 @@ def main(argv=None):
         return run_reference(args, ws, rank)
     if args.batch_singles > 0:
         return run_batch_singles(args)
+    if args.batch_overhead:
+        return run_batch_overhead(args)
     if args.fp64_peak:
         from paper_2305_13419_gb300 import twofluid as tf
         rates = [tf.fp64_fma_rate() for _ in range(3)]
