@@ -430,6 +430,7 @@ def run_ours(args, ws, rank, local):
         base["sample"] += " (a 256 x 256 x 128 block of the 1024 x 512 x 256 workload, PEC-closed)"
 
     adj = batch = extra = None
+    w_name = w.name
     del w
     if rank == 0 and not args.no_configs:
         two = args.two_step != "off"
@@ -440,7 +441,7 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.no_adjoint:
         adj = run_adjoint(args)
     if rank == 0 and not args.no_batch:
-        batch = run_batch(args, plain_small or value / ws)
+        batch = run_batch(args, plain_small or value / ws, "cpw-512x256x128" if plain_small else w_name)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -493,7 +494,7 @@ def run_adjoint(args):
             "includes": "forward with checkpoints, per-segment recompute, adjoint steps, gradient reduction"}
 
 
-def run_batch(args, plain_gcells):
+def run_batch(args, plain_gcells, plain_workload="cpw-512x256x128"):
     """The batched workload: 64 CPW variants with axes from {96, 128, 160}.
     Headline: tf_batch_run, one launch per step over all 64 grids (one work
     list over all grids' items), 64 steps per CUDA graph, timed with CUDA
@@ -536,6 +537,8 @@ def run_batch(args, plain_gcells):
                                       "peak_source": peak_kind}}
     streams = [torch.cuda.Stream() for _ in range(8)]
     grids = [tf.Grid.from_workload(w, stream=streams[i % 8]) for i, w in enumerate(ws)]
+    for gg in grids:   # single steps, as in the batched launch (the autotuner's choice on grids this small)
+        gg.set_two_step(0)
     tf.batch_step(grids, 10)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -552,13 +555,13 @@ def run_batch(args, plain_gcells):
                        "timing": "host wall clock around the enqueue of all steps, device synchronised on both sides"}
     out["gcell_updates_per_s"] = out["one_launch"]["gcell_updates_per_s"]
     out["vs_plain_step"] = out["gcell_updates_per_s"] / plain_gcells
-    out["plain_step"] = {"workload": "cpw-512x256x128", "gcell_updates_per_s": plain_gcells}
+    out["plain_step"] = {"workload": plain_workload, "gcell_updates_per_s": plain_gcells}
     return out
 
 
 def run_batch_singles(args):
-    """The batch's grids stepped one at a time (each alone on the GPU): the
-    per-grid rate that the batched stepping is compared with."""
+    """The batch's grids stepped one at a time (each alone on the GPU, single
+    steps): the per-grid rate that the batched stepping is compared with."""
     import time
     import torch
     from paper_2305_13419_gb300 import twofluid as tf
@@ -566,6 +569,7 @@ def run_batch_singles(args):
     rows, cells, secs = [], 0, 0.0
     for w in W.cpw_batch()[:args.batch_singles]:
         g = tf.Grid.from_workload(w)
+        g.set_two_step(0)   # single steps, as in the batched launch
         g.step(20)
         g.sync()
         t0 = time.perf_counter()
