@@ -112,3 +112,32 @@ def test_null_handle_calls_fail_cleanly():
     assert L.tf_set_two_step(None, 1) == tf.TF_EINVAL
     assert L.tf_set_wait_limit(None, 0) == tf.TF_EINVAL
     assert tf.tf_strerror(tf.TF_ENONFINITE) == "non-finite field value"
+
+
+def _size_and_create(n, bc=("periodic", "periodic", "pec")):
+    d = _desc(n=n, bc=bc, cpml=(None, None, None))
+    h = C.c_void_p()
+    return tf.tf_workspace_size(d), d, h
+
+
+def test_largest_descriptor_grids_accepted_one_past_rejected():
+    """Work-item descriptors carry 20 bits of tile index and 20 bits of
+    plane: a grid with exactly 2^20 storage planes along z, or exactly 2^20
+    32 x 16 tiles, is accepted (its workspace is sized; nothing is
+    allocated), one plane or one tile column more is refused on the host
+    (TF_ENOTSUP), and more than 2^40 storage points is TF_EINVAL."""
+    L = tf.load()
+    size, _, _ = _size_and_create((4, 4, (1 << 20) - 1))          # 2^20 storage planes (walled z)
+    assert size > 0
+    size, d, h = _size_and_create((4, 4, 1 << 20))
+    assert size == 0
+    assert L.tf_create(C.byref(d), C.c_void_p(256), C.c_size_t(1 << 30), C.byref(h)) == tf.TF_ENOTSUP
+    # 32768 x 16384 storage columns: 1024 x 1024 tiles
+    size, _, _ = _size_and_create((32767, 16383, 1), bc=("pec", "pec", "pec"))
+    assert size > 0
+    size, d, h = _size_and_create((32768, 16383, 1), bc=("pec", "pec", "pec"))
+    assert size == 0
+    assert L.tf_create(C.byref(d), C.c_void_p(256), C.c_size_t(1 << 30), C.byref(h)) == tf.TF_ENOTSUP
+    size, d, h = _size_and_create((1 << 14, 1 << 14, 1 << 13), bc=("periodic", "periodic", "periodic"))
+    assert size == 0
+    assert L.tf_create(C.byref(d), C.c_void_p(256), C.c_size_t(1 << 30), C.byref(h)) == tf.TF_EINVAL
