@@ -41,9 +41,11 @@
 // memory of the staged axis comes from shared memory, that of any further
 // slab axis from global memory; a tile-plane whose cells are all alike uses
 // one precomputed {ca, cb, cj, 1/mu} record, the others per-point
-// coefficients set with the materials.  The plane body is compiled twice:
-// work items that meet a source, a Mur plane, a second CPML axis or varying
-// mu take the full body, all others a body without that code.
+// coefficients set with the materials.  The plane body is compiled three
+// times: work items that meet a source, a Mur plane or varying mu take the
+// full body, items whose planes meet a second CPML axis (and nothing else
+// of those) a body with the further CPML axes only, all others a body
+// without that code.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <math.h>
@@ -244,19 +246,20 @@ __device__ __forceinline__ void src_range(const Sources& S, const Tile& t, int& 
     }
 }
 
-// an item needs the full plane loop: varying mu, a second CPML axis on one
-// of its planes, a source plane or a Mur plane
-__device__ __forceinline__ bool item_is_rare(const Params& P, const Sources& S, bool mur, const Tile& t) {
-    if (!P.uniform_mu) return true;
+// the plane loop an item runs: 2 (the full one) with varying mu, a source
+// plane or a Mur plane; else 1 (further CPML axes only) with a second CPML
+// axis on one of its planes; else 0
+__device__ __forceinline__ int item_kind(const Params& P, const Sources& S, bool mur, const Tile& t) {
+    if (!P.uniform_mu) return 2;
     const int ka = t.ks < 0 ? 0 : t.ks, kb = t.kz1 - 1;   // planes of the item (periodic wrap: z has no slab)
+    int sk0, sk1;
+    src_range(S, t, sk0, sk1);
+    if (sk1 > sk0 && ((kb >= sk0 && ka < sk1) || (t.ks < 0 && P.N[2] - 1 >= sk0 && P.N[2] - 1 < sk1))) return 2;
+    if (mur && ((ka <= 1 && 1 <= kb) || (ka <= P.n[2] - 1 && P.n[2] - 1 <= kb))) return 2;
     const bool sx = P.L[0] > 0 && (t.x0 - 1 < P.L[0] || t.x0 + kSX - 1 >= P.n[0] - P.L[0]);
     const bool sy = P.L[1] > 0 && (t.y0 - 1 < P.L[1] || t.y0 + kSY - 1 >= P.n[1] - P.L[1]);
     const bool sz = P.L[2] > 0 && (ka < P.L[2] || kb >= P.n[2] - P.L[2]);
-    if ((int)sx + (int)sy + (int)sz >= 2) return true;
-    int sk0, sk1;
-    src_range(S, t, sk0, sk1);
-    if (sk1 > sk0 && ((kb >= sk0 && ka < sk1) || (t.ks < 0 && P.N[2] - 1 >= sk0 && P.N[2] - 1 < sk1))) return true;
-    return mur && ((ka <= 1 && 1 <= kb) || (ka <= P.n[2] - 1 && P.n[2] - 1 <= kb));
+    return (int)sx + (int)sy + (int)sz >= 2 ? 1 : 0;
 }
 
 }  // namespace
@@ -600,11 +603,12 @@ __global__ void __launch_bounds__(kThreads, 2)
         float cfnext = 0.f;                                 // and this thread's coefficient entry
         f2 bpx = 0, bpy = 0;     // B^{n+1/2}(k-1) at the own pair (z differences)
         f2 elo0 = 0, elo1 = 0;   // E^n on the low Mur wall
-        // one plane, compiled twice: items that meet a source, a Mur plane, a
-        // second CPML axis or varying mu run the full version, all others a
-        // version without that code
-        auto plane = [&](auto rare_tag, int qq) -> bool {   // false: a copy never landed
-            constexpr bool kRare = decltype(rare_tag)::value;
+        // one plane, compiled for the three item kinds (item_kind): the full
+        // version (sources, Mur planes, varying mu, further CPML axes), the
+        // further CPML axes only, and neither
+        auto plane = [&](auto kind_tag, int qq) -> bool {   // false: a copy never landed
+            constexpr int kKind = decltype(kind_tag)::value;
+            constexpr bool kSecOn = kKind >= 1, kFull = kKind == 2;
             const int k = plane_of(P, t, qq);
             const bool doE = t.ks + qq >= kz0;   // E update (and B store) at this plane
             const unsigned long long g0 = seq0 + qq, g1 = g0 + 1;
@@ -614,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const float4 rec = s_rec[cur][qq];
             const int sax = (int)((f >> kFSaxShift) & 3u) - 1;
             const bool coef = (f & kFCoef) != 0, zlo = (f & kFZlo) != 0;
-            const unsigned sec = kRare ? (f / kFSec0) & 7u : 0u;
+            const unsigned sec = kSecOn ? (f / kFSec0) & 7u : 0u;
             const bool masked = !open || zlo;
             const unsigned mk = zlo ? m & ~kMaskZlo : m, hmk = zlo ? hm & ~kMaskZlo : hm;
             float(*bn)[kBY][kBX] = bplanes[it & 1];
@@ -680,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
             f2 ho0 = 0, ho1 = 0, ho2 = 0, ho3 = 0;   // halo: old memories of the first two further axes
             unsigned hin = 0;                        // halo: bits 2a, 2a + 1: point inside the slab of axis a
-            if (kRare && sec) {   // CPML memories of the further slab axes: into L1 while the stage lands
+            if (kSecOn && sec) {   // CPML memories of the further slab axes: into L1 while the stage lands
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     if (!((sec >> a) & 1u)) continue;
@@ -730,7 +734,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             // ------------------------------------------------ B phase
             f2 p0, p1;
             P3 nb = b_pair(P, s0, s1, j, i0, sax, bB, cB, p0, p1);
-            if (kRare && sec) {   // CPML memory of further slab axes, both points at once
+            if (kSecOn && sec) {   // CPML memory of further slab axes, both points at once
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     if (!((sec >> a) & 1u)) continue;
@@ -773,7 +777,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (hal) {
                 f2 hp0, hp1;
                 P3 h = b_pair(P, s0, s1, hj, hi0, sax, hbB, hcB, hp0, hp1);
-                if (kRare && sec) {   // further slab axes of the halo pair (their new memories: formed by the owner)
+                if (kSecOn && sec) {   // further slab axes of the halo pair (their new memories: formed by the owner)
                     int n = 0;
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
@@ -832,7 +836,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 f2 hx = nb.x, hx_zm = bpx, hx_ym = ld2(&bn[0][j - 1][i0]);
                 f2 hy = nb.y, hy_zm = bpy, hy_xm = pk(bn[1][j][i0 - 1], lo(nb.y));
                 f2 hz = nb.z, hz_ym = ld2(&bn[2][j - 1][i0]), hz_xm = pk(bn[2][j][i0 - 1], lo(nb.z));
-                const bool imuf = kRare && (f & kFImu);
+                const bool imuf = kFull && (f & kFImu);
                 if (!P.uniform_mu && !imuf) {   // one record: one mu
                     const f2 w = pk(rec.w, rec.w);
                     hx = mul2(hx, w); hx_zm = mul2(hx_zm, w); hx_ym = mul2(hx_ym, w);
@@ -893,7 +897,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     cx = sub2(cx, q0);
                     cy = add2(cy, q1);
                 }
-                if (kRare && sec) {   // further slab axes, both points at once
+                if (kSecOn && sec) {   // further slab axes, both points at once
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         if (!((sec >> a) & 1u)) continue;
@@ -935,7 +939,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 f2 n0 = fma2(cb0, sub2(cx, jt0), mul2(ca0, em0));
                 f2 n1 = fma2(cb1, sub2(cy, jt1), mul2(ca1, em1));
                 f2 n2 = fma2(cb2, sub2(cz, jt2), mul2(ca2, em2));
-                if (kRare && (f & kFSrc)) {   // soft sources
+                if (kFull && (f & kFSrc)) {   // soft sources
                     float ax0 = 0.f, ax1 = 0.f, ay0 = 0.f, ay1 = 0.f, az0 = 0.f, az1 = 0.f;
                     for (int s = 0; s < S.n; ++s) {
                         if (gy < S.lo[s][1] || gy >= S.hi[s][1] || k < S.lo[s][2] || k >= S.hi[s][2]) continue;
@@ -982,7 +986,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const f2 sum = add2(add2(n0, n1), n2);
                 if (!isfinite(lo(sum) + (v1 ? hi(sum) : 0.f))) atomicOr(P.status, kStatusNonFinite);
                 // first-order Mur on the z walls: E_w^{n+1} = E_i^n + M (E_i^{n+1} - E_w^n)
-                if (kRare && (f & (kFMurLo | kFMurHi))) {
+                if (kFull && (f & (kFMurLo | kFMurHi))) {
 #pragma unroll
                     for (int p = 0; p < 2; ++p) {
                         if (!(p ? v1 : v0)) continue;
@@ -1000,7 +1004,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     }
                 }
             }
-            if (kRare && zlo) {
+            if (kFull && zlo) {
                 elo0 = ld2(&s0.e[0][j][i0]);
                 elo1 = ld2(&s0.e[1][j][i0]);
             }
@@ -1008,9 +1012,11 @@ __global__ void __launch_bounds__(kThreads, 2)
             bpy = nb.y;
             return true;
         };
-        const bool rare = item_is_rare(P, S, mur, t);
+        const int kind = item_kind(P, S, mur, t);
         for (int qq = 0; qq < nq - 1; ++qq, ++it) {
-            const bool ok = rare ? plane(std::true_type{}, qq) : plane(std::false_type{}, qq);
+            const bool ok = kind == 0   ? plane(std::integral_constant<int, 0>{}, qq)
+                            : kind == 1 ? plane(std::integral_constant<int, 1>{}, qq)
+                                        : plane(std::integral_constant<int, 2>{}, qq);
             if (!ok) {
                 aborted = true;
                 break;
@@ -1188,7 +1194,7 @@ __global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Source
         len = min(kChunk, O.kend - kz0);
     };
     auto rare_of = [&](int tile, int kz0, int len) {
-        return item_is_rare(P, S, mur, tile_of(P, O, make_item(tile, kz0, len)));
+        return item_kind(P, S, mur, tile_of(P, O, make_item(tile, kz0, len))) != 0;
     };
     auto scan = [&](int* v) {   // inclusive prefix sum over the block
         for (int off = 1; off < 1024; off <<= 1) {
