@@ -436,16 +436,14 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
             delete h;
             return TF_ECUDA;
         }
-        // one resident CTA per slot, but no more than half the items: a small
-        // grid then leaves SMs to grids stepping on other streams.  A grid
+        // one resident CTA per slot (no more than the units of work).  A grid
         // with fewer items than slots goes out in kSub-plane pieces.
         const long long slots = (long long)sms * per_sm;
         h->slots = (int)slots;
         h->slots2 = sms * per_sm2;
         h->fine = items < slots;
         const long long units = h->fine ? items * ((kChunk + kSub - 1) / kSub) : items;
-        long long nb = slots, half = (units + 1) / 2;
-        if (half < nb) nb = half;
+        const long long nb = units < slots ? units : slots;
         h->step_blocks = (int)(nb > 0 ? nb : 1);
     }
     // zero everything but the profiles, then vacuum materials
@@ -992,18 +990,25 @@ tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, void* scratch
         }
         Sources S;
         fill_sources(h, S);
-        if (refresh_order(h, S) != cudaSuccess ||
-            cudaMemcpy(items + ntot, h->O.order, sizeof(long long) * (size_t)h->O.nitems, cudaMemcpyDeviceToHost) !=
-                cudaSuccess) {
+        // the grid's whole items, slow ones first, none cut into pieces (the
+        // batch's one list balances the launch), made in the scratch's list
+        // area and read back
+        long long* tmp = (long long*)((char*)scratch + BL.off_order);
+        int* dcount = (int*)(h->ws + h->L.off_misc + 192);
+        int cnt = 0;
+        if (launch_item_order(h->P, h->O, S, 0, 0, tmp, dcount, h->stream) != cudaSuccess ||
+            cudaMemcpyAsync(&cnt, dcount, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess || cnt < 0 || ntot + cnt > BL.max_items ||
+            cudaMemcpy(items + ntot, tmp, sizeof(long long) * (size_t)cnt, cudaMemcpyDeviceToHost) != cudaSuccess) {
             rc = TF_ECUDA;
             break;
         }
-        for (long long k = ntot; k < ntot + h->O.nitems; ++k) {
+        for (long long k = ntot; k < ntot + cnt; ++k) {
             rare[k] = rare_item(h, S, item_tile(items[k]), item_kz0(items[k]), item_len(items[k])) ? 1 : 0;
             items[k] = item_with_grid(items[k], i);
             nrare += rare[k];
         }
-        ntot += h->O.nitems;
+        ntot += cnt;
         BatchGrid& g = G[i];
         memcpy(&g.tm, h->tmap[0], sizeof(TMaps));
         g.P[0] = h->P;
