@@ -795,7 +795,7 @@ cudaError_t refresh_order(tf_ctx* h, const Sources& S) {
     // the last plain items of the order, one per CTA, also go out in pieces:
     // the CTAs then run out of work at nearly the same time
     const int tail = h->fine ? (int)items : h->step_blocks;
-    cudaError_t e = launch_item_order(h->P, h->O, S, split, tail, (long long*)h->O.order, dcount, h->stream);
+    cudaError_t e = launch_item_order(h->P, h->O, S, split, tail, kChunk, (long long*)h->O.order, dcount, h->stream);
     int n = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&n, dcount, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -996,7 +996,7 @@ tf_status tf_batch_run(const tf_handle* hs, int n, int64_t nsteps, void* scratch
         long long* tmp = (long long*)((char*)scratch + BL.off_order);
         int* dcount = (int*)(h->ws + h->L.off_misc + 192);
         int cnt = 0;
-        if (launch_item_order(h->P, h->O, S, 0, 0, tmp, dcount, h->stream) != cudaSuccess ||
+        if (launch_item_order(h->P, h->O, S, 0, 0, kItemMax, tmp, dcount, h->stream) != cudaSuccess ||
             cudaMemcpyAsync(&cnt, dcount, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
             cudaStreamSynchronize(h->stream) != cudaSuccess || cnt < 0 || ntot + cnt > BL.max_items ||
             cudaMemcpy(items + ntot, tmp, sizeof(long long) * (size_t)cnt, cudaMemcpyDeviceToHost) != cudaSuccess) {

@@ -82,15 +82,20 @@ constexpr int kSX = kTX, kSY = kTY;          // tile stride
 constexpr int kEX = kTX + 8, kEY = kTY + 2;  // E box: x0-4 .. x0+35, y0-1 .. y0+kTY
 constexpr int kBX = kTX + 4, kBY = kTY + 1;  // B / psi_B box: x0-4 .. x0+31, y0-1 .. y0+kTY-1
 constexpr int kStages = 4;                   // planes in flight per CTA
-constexpr int kChunk = 8;                    // z planes per work item
+constexpr int kChunk = 8;                    // z planes per work item of a grid stepped alone
+constexpr int kItemMax = 16;                 // z planes per work item at most (a batch's items)
 // The last plane an item pulls is only ever the upper plane of its last
 // step, so the ring must hold the two planes the next item starts with
 // while that one is still in use: four stages at least.
 static_assert(kStages >= 4, "the ring must reach two planes into the next item");
 
-// per-item CPML coefficient table: kBX columns, kBY rows, kChunk + 2 planes per profile
-constexpr int kCfY = kBX, kCfZ = kBX + kBY, kCfN = 64;
-static_assert(kCfZ + kChunk + 2 <= kCfN && 4 * kCfN <= kTX * (kTY / kRows), "one table entry per thread");
+// per-item CPML coefficient table: kBX columns, kBY rows, kItemMax + 2 planes
+// per profile; every thread loads one entry, the kCfExtra past its 256 are
+// loaded by the second warp's threads
+constexpr int kCfY = kBX, kCfZ = kBX + kBY, kCfN = 72;
+constexpr int kCfExtra = 4 * kCfN - kTX * (kTY / kRows);
+static_assert(kCfZ + kItemMax + 2 <= kCfN && kCfExtra >= 0 && kCfExtra <= 32, "table entries per thread");
+static_assert(kItemMax + 1 <= 32, "the records of an item are loaded by the first warp");
 constexpr int kSub = 2;                      // planes per piece of a work item that takes the full loop
 // a work item is a 64-bit descriptor: tile (bits 0-19), first plane (20-39),
 // planes (40-47); -1 marks the end of the work
@@ -386,7 +391,8 @@ cudaError_t launch_adjoint_cells(const Params& P, const AdjState& A, float dt_c0
                                  float* g_lam, cudaStream_t stream);
 
 // order in which k_step hands out its work items (items needing the full plane loop first)
-cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int tail, long long* order,
+cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int tail, int chunk,
+                              long long* order,
                               int* count, cudaStream_t st);
 int step_blocks_per_sm();
 cudaError_t launch_field_stats(const float* f, int n0, int n1, int n2, int pitch, long long plane, double scale,

@@ -323,8 +323,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     unsigned long long* bar =
         reinterpret_cast<unsigned long long*>(smem_raw + kStages * sizeof(StageBuf) + 2 * kBPlaneBytes);
     __shared__ long long s_item[2];             // current and next work item (-1: none)
-    __shared__ float4 s_rec[2][kChunk + 2];     // material record of each plane of the two items
-    __shared__ unsigned s_flag[2][kChunk + 2];  // plane flags
+    __shared__ float4 s_rec[2][kItemMax + 2];     // material record of each plane of the two items
+    __shared__ unsigned s_flag[2][kItemMax + 2];  // plane flags
     // CPML coefficients of the two items (zero outside the slabs): per profile
     // (b_B, c_B, b_E, c_E) the tile's columns x0-4 .. x0+31, rows y0-1 ..
     // y0+15 and the item's planes
@@ -357,15 +357,9 @@ __global__ void __launch_bounds__(kThreads, 2)
         return (d >= 0 && d < nitems) ? __ldg(order + d) : -1LL;
     };
     // the records of an item: loaded by threads < nq - 1 ...
-    auto rec_load = [&](long long item, float4& r, float& cf) {
-        if (item < 0) return;
-        const GridRef g = gridref(item);
-        const Params& P = *g.P;
-        const StepOut& O = *g.O;
-        const Tile t = tile_of(P, O, item);
-        if (tid < t.nq - 1) r = __ldg(O.tilemat + (long long)(t.by * O.ntx + t.bx) * P.N[2] + plane_of(P, t, tid));
-        // one coefficient table entry per thread: profile tid / kCfN, entry tid % kCfN
-        const int pr = tid / kCfN, e = tid % kCfN;
+    // (entry u of the coefficient table: profile u / kCfN, entry u % kCfN)
+    auto cf_entry = [&](const Params& P, const Tile& t, int u) -> float {
+        const int pr = u / kCfN, e = u % kCfN;
         int a = -1, pos = 0;
         if (e < kCfY) {
             a = 0;
@@ -377,16 +371,27 @@ __global__ void __launch_bounds__(kThreads, 2)
             a = 2;
             pos = plane_of(P, t, e - kCfZ);
         }
-        cf = 0.f;
-        if (a >= 0 && slab_pos(P, a, pos)) {
-            const float* pf = pr == 0 ? P.pbB[a] : pr == 1 ? P.pcB[a] : pr == 2 ? P.pbE[a] : P.pcE[a];
-            cf = __ldg(pf + pos);
-        }
+        if (a < 0 || !slab_pos(P, a, pos)) return 0.f;
+        const float* pf = pr == 0 ? P.pbB[a] : pr == 1 ? P.pcB[a] : pr == 2 ? P.pbE[a] : P.pcE[a];
+        return __ldg(pf + pos);
+    };
+    auto rec_load = [&](long long item, float4& r, float& cf) {
+        if (item < 0) return;
+        const GridRef g = gridref(item);
+        const Params& P = *g.P;
+        const StepOut& O = *g.O;
+        const Tile t = tile_of(P, O, item);
+        if (tid < t.nq - 1) r = __ldg(O.tilemat + (long long)(t.by * O.ntx + t.bx) * P.N[2] + plane_of(P, t, tid));
+        // one coefficient table entry per thread; the second warp's threads,
+        // which load no record, carry one more in r.x
+        cf = cf_entry(P, t, tid);
+        if (tid >= 32 && tid < 32 + kCfExtra) r.x = cf_entry(P, t, kThreads + tid - 32);
     };
     // ... and stored with the plane flags
     auto rec_store = [&](long long item, int slot, const float4& r, float cf) {
         if (item < 0) return;
         (&s_cf[slot][0][0])[tid] = cf;
+        if (tid >= 32 && tid < 32 + kCfExtra) (&s_cf[slot][0][0])[kThreads + tid - 32] = r.x;
         const GridRef g = gridref(item);
         const Params& P = *g.P;
         const StepOut& O = *g.O;
@@ -1181,17 +1186,18 @@ cudaError_t launch_step_advance(int* step, cudaStream_t st) {
 // CTAs at work at one time then share halos in L2), the last `tail` of them
 // cut into kSub-plane pieces so that the CTAs run out of work together.
 // One CTA; writes the descriptors and their count.
-__global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Sources S, int split, int tail, long long* order,
+__global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Sources S, int split, int tail, int chunk,
+                                                    long long* order,
                                                     int* count) {
     __shared__ int s_slow[1024], s_fast[1024], s_tail[1024];
-    const int n = O.ntx * O.nty * O.nch, ntiles = O.ntx * O.nty;
+    const int ntiles = O.ntx * O.nty, n = ntiles * ((O.kend + chunk - 1) / chunk);
     const int per = (n + 1023) / 1024;
     const int a = min((int)threadIdx.x * per, n), b = min(a + per, n);
     const bool mur = P.bc[2] == TF_BC_MUR;
-    auto chunk = [&](int d, int& tile, int& kz0, int& len) {
+    auto item_at = [&](int d, int& tile, int& kz0, int& len) {
         tile = d % ntiles;
-        kz0 = (d / ntiles) * kChunk;
-        len = min(kChunk, O.kend - kz0);
+        kz0 = (d / ntiles) * chunk;
+        len = min(chunk, O.kend - kz0);
     };
     auto rare_of = [&](int tile, int kz0, int len) {
         return item_kind(P, S, mur, tile_of(P, O, make_item(tile, kz0, len))) != 0;
@@ -1207,7 +1213,7 @@ __global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Source
     int ns = 0, nf = 0;
     for (int d = a; d < b; ++d) {
         int tile, kz0, len;
-        chunk(d, tile, kz0, len);
+        item_at(d, tile, kz0, len);
         if (rare_of(tile, kz0, len))
             ns += split ? (len + kSub - 1) / kSub : 1;
         else
@@ -1225,7 +1231,7 @@ __global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Source
         int rank = s_fast[threadIdx.x] - nf;
         for (int d = a; d < b; ++d) {
             int tile, kz0, len;
-            chunk(d, tile, kz0, len);
+            item_at(d, tile, kz0, len);
             if (rare_of(tile, kz0, len)) continue;
             if (rank >= cut) nt += (len + kSub - 1) / kSub;
             ++rank;
@@ -1239,7 +1245,7 @@ __global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Source
     int c = total_slow + cut + s_tail[threadIdx.x] - nt;  // position of its first tail piece
     for (int d = a; d < b; ++d) {
         int tile, kz0, len;
-        chunk(d, tile, kz0, len);
+        item_at(d, tile, kz0, len);
         if (rare_of(tile, kz0, len)) {
             const int piece = split ? kSub : len;
             for (int k = kz0; k < kz0 + len; k += piece) order[r++] = make_item(tile, k, min(piece, kz0 + len - k));
@@ -1255,9 +1261,10 @@ __global__ void __launch_bounds__(1024) k_item_order(Params P, StepOut O, Source
     if (threadIdx.x == 1023) *count = total_slow + cut + s_tail[1023];
 }
 
-cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int tail, long long* order,
-                              int* count, cudaStream_t st) {
-    k_item_order<<<1, 1024, 0, st>>>(P, O, S, split, tail, order, count);
+cudaError_t launch_item_order(const Params& P, const StepOut& O, const Sources& S, int split, int tail, int chunk,
+                              long long* order, int* count, cudaStream_t st) {
+    if (chunk < 1 || chunk > kItemMax) return cudaErrorInvalidValue;
+    k_item_order<<<1, 1024, 0, st>>>(P, O, S, split, tail, chunk, order, count);
     return cudaGetLastError();
 }
 
