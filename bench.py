@@ -331,14 +331,15 @@ def config_block(state_bytes=None):
     return c
 
 
-def roofline_of(w, g, kt, planes=16):
+def roofline_of(w, g, kt, planes=16, item_planes=8):
     """Roofline of the step kernels from their algorithmic bytes per launch
     over their mean event-timed launch durations, against the measured HBM
     peak.  With two-step passes the two-step kernel (the interior box, two
     steps per launch) and the single-step kernel (the rest of the grid, one
     step per launch) are listed apart; the dominant one (larger share of the
-    run's kernel time) heads the object.  `planes`: the two-step work-item
-    length the run used (the ncu traffic is keyed by it)."""
+    run's kernel time) heads the object.  `planes`, `item_planes`: the
+    two-step and single-step work-item lengths the run used (the ncu
+    traffic is keyed by them)."""
     peak, peak_kind = hbm_peak()
     (lo, hi), active = g.two_step_box()
     two = "step2" in kt
@@ -353,7 +354,8 @@ def roofline_of(w, g, kt, planes=16):
         kernels["k_step"] = {"algorithmic_bytes": ab["step"], "points": ab["points"], "steps_per_launch": 1,
                              "ms": kt["step"][0], "launches": kt["step"][1]}
     # ncu traffic keys: the launch kind on the workload
-    keys = {"k_step2": f"{w.name}/two-step-{planes}", "k_step": f"{w.name}/shell" if two else w.name}
+    keys = {"k_step2": f"{w.name}/two-step-{planes}",
+            "k_step": f"{w.name}/shell-items-{item_planes}" if two else f"{w.name}/items-{item_planes}"}
     for k, v in kernels.items():
         v["achieved_GBps"] = v["algorithmic_bytes"] / (v["ms"] * 1e-3) / 1e9
         v["frac"] = v["achieved_GBps"] / peak
@@ -395,6 +397,10 @@ def run_ours(args, ws, rank, local):
     elif not args.no_autotune:   # the temporal-block depth and item length, from measured runs
         from paper_2305_13419_gb300 import autotune
         tuning = autotune.tune_grid(g, steps=args.autotune_steps)
+    if args.item_planes:   # a fixed single-step item length (reproducible profiling runs)
+        g.set_item_planes(args.item_planes)
+        if tuning is not None:
+            tuning["item_planes"] = args.item_planes
     N = g.N
 
     # device-timed throughput: inputs resident in HBM, K steps between
@@ -412,7 +418,8 @@ def run_ours(args, ws, rank, local):
     g.sync()
     ms_max = max_over_ranks(dist, ms, dev)
     value = aggregate(w.ncells, args.steps, ms_max, ws)
-    ab, roof = roofline_of(w, g, kt, planes=tuning["best"] if tuning and tuning["best"] else 16)
+    ab, roof = roofline_of(w, g, kt, planes=tuning["best"] if tuning and tuning["best"] else 16,
+                           item_planes=tuning["item_planes"] if tuning else (args.item_planes or 8))
     state_bytes = (9 + 3) * 4 * ab["points"]
     launches = sum(v[1] for v in kt.values())
     g.close()
@@ -422,7 +429,7 @@ def run_ours(args, ws, rank, local):
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, w, dev)
+        e2e = run_e2e(args, w, dev, tuning)
 
     base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -480,6 +487,7 @@ def run_adjoint(args):
     g = tf.Grid.from_workload(w)
     if tuning is not None:
         g.set_two_step(tuning["best"])
+        g.set_item_planes(tuning["item_planes"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     J, ge, gl = g.adjoint(args.adjoint_steps, 0, 0, segment=args.adjoint_segment)
@@ -646,7 +654,8 @@ def run_config(w, steps, warmup=5, two_step=True, autotune_steps=0):
     torch.cuda.synchronize()
     kt, ms = g.step_timed(steps, with_total=True)
     g.sync()
-    _, roof = roofline_of(w, g, kt, planes=tuning["best"] if tuning and tuning["best"] else 16)
+    _, roof = roofline_of(w, g, kt, planes=tuning["best"] if tuning and tuning["best"] else 16,
+                          item_planes=tuning["item_planes"] if tuning else 8)
     g.close()
     del g
     torch.cuda.empty_cache()
@@ -757,11 +766,12 @@ def run_autotune_table(args):
     return 0
 
 
-def run_e2e(args, w, dev):
+def run_e2e(args, w, dev, tuning=None):
     """Same metric through the public API from host memory: the timed region
     uploads the material maps from pinned host buffers, runs the K steps and
     reads back both probe DFTs and the integer-level Ex field into pinned
-    host memory."""
+    host memory.  The grid takes the settings the autotuner chose for the
+    device-timed run (`tuning`), as a user applying its table would."""
     import torch
     from paper_2305_13419_gb300 import twofluid as tf
     g = tf.Grid(w.n, w.d, w.theta, w.bc, w.cpml, courant=w.courant, device=dev)
@@ -776,6 +786,14 @@ def run_e2e(args, w, dev):
         g.add_source(s.comp, s.lo, s.hi, s.amp, s.kind, s.f, s.t0, s.tw)
     for p in w.probes:
         g.add_probe(p.comp, p.p, p.freqs, p.n0)
+    if args.two_step == "off":
+        g.set_two_step(0)
+    elif tuning is not None:
+        g.set_two_step(tuning["best"])
+    if tuning is not None:
+        g.set_item_planes(tuning["item_planes"])
+    elif args.item_planes:
+        g.set_item_planes(args.item_planes)
     import ctypes as C
     L = tf.load()
     torch.cuda.synchronize()
@@ -806,6 +824,8 @@ def main(argv=None):
                     help="tune every workload class (slab, CPWs, adjoint grid, the batch's size classes) and "
                          "write the table to this JSON path (one JSON line printed)")
     ap.add_argument("--autotune-steps", type=int, default=20, help="steps timed per autotuner candidate")
+    ap.add_argument("--item-planes", type=int, default=0,
+                    help="planes per single-step work item of the timed grid (8..16; default: the autotuner's or 8)")
     ap.add_argument("--workload", choices=("large", "cpw"), default="large",
                     help="the timed workload: the 1024 x 512 x 256 CPW (default) or the 512 x 256 x 128 one")
     ap.add_argument("--two-step", choices=("auto", "off"), default="auto",

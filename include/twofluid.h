@@ -199,6 +199,14 @@ tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t*
 tf_status tf_set_two_step(tf_handle h, int planes);
 tf_status tf_two_step_box(tf_handle h, int lo[3], int hi[3], int* active);
 
+/* Planes per work item of the single-step kernel (its items, and the
+ * shell's items in two-step passes): 8 .. 16 (8 by default; other
+ * values TF_EINVAL).  Longer items re-read fewer z halo planes and change
+ * items less often; shorter ones balance a small grid's few items over the
+ * CTAs better.  A tuning switch (the project's autotuner sets it per grid):
+ * results do not change. */
+tf_status tf_set_item_planes(tf_handle h, int planes);
+
 /* The stepping kernels wait on an mbarrier for every plane they stage; each
  * wait polls it at most `polls` times (default 2^22, far beyond a copy's
  * latency).  A wait that runs out latches TF_ETIMEOUT for tf_sync(): the

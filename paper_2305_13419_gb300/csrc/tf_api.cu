@@ -146,6 +146,7 @@ struct tf_ctx {
     unsigned long long* ctr_t;
     unsigned long long base_t;
     int two_step_on;    // two-step passes allowed (tf_set_two_step; on by default)
+    int item_planes;    // planes per single-step work item (tf_set_item_planes)
     int tb_len;         // planes per two-step work item
     int ppos[TF_MAX_PROBES][3];   // probe points (storage coordinates)
     Probes R;
@@ -421,6 +422,7 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
     h->base_t = 0;
     h->two_step_on = 1;
     h->tb_len = kTBLenMax;
+    h->item_planes = kChunk;
     P.status = h->status;
     P.wait_polls = kSpinLimit;
     {
@@ -715,8 +717,8 @@ cudaError_t build_two_step_lists(tf_ctx* h, const Sources& S) {
     bool ok = true;
     for (int pass = 0; pass < 2; ++pass) {   // pass 0 counts the pieces, pass 1 lists them
         const bool split = pass == 1 && npieces < 8LL * h->slots;
-        for (int kz = 0; kz < L.kend; kz += kChunk) {
-            const int ke = kz + kChunk < L.kend ? kz + kChunk : L.kend;
+        for (int kz = 0; kz < L.kend; kz += h->item_planes) {
+            const int ke = kz + h->item_planes < L.kend ? kz + h->item_planes : L.kend;
             for (int ty = 0; ty < L.nty; ++ty)
                 for (int tx = 0; tx < L.ntx; ++tx) {
                     const int tile = ty * L.ntx + tx;
@@ -790,12 +792,13 @@ cudaError_t refresh_order(tf_ctx* h, const Sources& S) {
     if (!h->order_dirty) return cudaSuccess;
     int* dcount = (int*)(h->ws + h->L.off_misc + 192);
     // fewer than 8 (tile, chunk) items per CTA: cut the slow ones into pieces
-    const long long items = (long long)h->L.ntx * h->L.nty * h->L.nch;
+    const long long items = (long long)h->L.ntx * h->L.nty * ((h->L.kend + h->item_planes - 1) / h->item_planes);
     const int split = items < 8LL * h->step_blocks;
     // the last plain items of the order, one per CTA, also go out in pieces:
     // the CTAs then run out of work at nearly the same time
     const int tail = h->fine ? (int)items : h->step_blocks;
-    cudaError_t e = launch_item_order(h->P, h->O, S, split, tail, kChunk, (long long*)h->O.order, dcount, h->stream);
+    cudaError_t e =
+        launch_item_order(h->P, h->O, S, split, tail, h->item_planes, (long long*)h->O.order, dcount, h->stream);
     int n = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&n, dcount, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -847,6 +850,15 @@ tf_status tf_set_two_step(tf_handle h, int planes) {
     if (planes != 0 && planes != h->tb_len) {
         h->tb_len = planes;
         h->order_dirty = 1;   // the box's work list is cut again
+    }
+    return TF_OK;
+}
+
+tf_status tf_set_item_planes(tf_handle h, int planes) {
+    if (!h || planes < kChunk || planes > kItemMax) return TF_EINVAL;
+    if (planes != h->item_planes) {
+        h->item_planes = planes;
+        h->order_dirty = 1;   // the work lists are cut again
     }
     return TF_OK;
 }

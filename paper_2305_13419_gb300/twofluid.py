@@ -26,7 +26,7 @@ TF_MAX_PROBES, TF_MAX_FREQS, TF_MAX_SOURCES = 16, 64, 16
 EXPORTS = ["tf_workspace_size", "tf_create", "tf_destroy", "tf_storage_dims", "tf_get_time", "tf_get_dt",
            "tf_set_materials", "tf_set_field", "tf_add_source", "tf_add_probe", "tf_step", "tf_sync",
            "tf_read_probe_dft", "tf_read_probe_series", "tf_read_field", "tf_fit_q", "tf_strerror",
-           "tf_step_timed", "tf_set_two_step", "tf_two_step_box", "tf_set_wait_limit", "tf_field_stats", "tf_field_stats_noalloc",
+           "tf_step_timed", "tf_set_two_step", "tf_two_step_box", "tf_set_wait_limit", "tf_set_item_planes", "tf_field_stats", "tf_field_stats_noalloc",
            "tf_checkpoint_size",
            "tf_checkpoint_save", "tf_checkpoint_load", "tf_adjoint_scratch_size", "tf_adjoint_run", "tf_batch_step",
            "tf_batch_scratch_size", "tf_batch_run",
@@ -88,7 +88,7 @@ def load(build_if_missing: bool = True):
                        ("tf_step", [vp, C.c_int64]), ("tf_sync", [vp]),
                        ("tf_step_timed", [vp, C.c_int64, dp, C.POINTER(C.c_int64), C.c_int, dp]),
                        ("tf_set_two_step", [vp, C.c_int]), ("tf_two_step_box", [vp, ip, ip, ip]),
-                       ("tf_set_wait_limit", [vp, C.c_int64]),
+                       ("tf_set_wait_limit", [vp, C.c_int64]), ("tf_set_item_planes", [vp, C.c_int]),
                        ("tf_read_probe_dft", [vp, C.c_int, dp, dp]),
                        ("tf_read_probe_series", [vp, C.c_int, dp, C.c_int64]),
                        ("tf_read_field", [vp, C.c_int, fp, C.c_int]),
@@ -468,6 +468,11 @@ class Grid:
         if planes is True:
             planes = 16
         _check(load().tf_set_two_step(self.h, int(planes or 0)), "tf_set_two_step")
+
+    def set_item_planes(self, planes: int):
+        """Planes per single-step work item (8 .. 16; a tuning switch: the
+        results do not change)."""
+        _check(load().tf_set_item_planes(self.h, int(planes)), "tf_set_item_planes")
 
     def set_wait_limit(self, polls):
         """Polls of a staged plane's mbarrier before the stepping kernels give

@@ -111,6 +111,7 @@ def test_null_handle_calls_fail_cleanly():
     assert L.tf_destroy(None) == tf.TF_EINVAL
     assert L.tf_set_two_step(None, 1) == tf.TF_EINVAL
     assert L.tf_set_wait_limit(None, 0) == tf.TF_EINVAL
+    assert L.tf_set_item_planes(None, 8) == tf.TF_EINVAL
     assert tf.tf_strerror(tf.TF_ENONFINITE) == "non-finite field value"
 
 

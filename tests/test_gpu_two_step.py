@@ -111,3 +111,33 @@ def test_two_step_item_lengths_give_the_same_bits(planes):
         with pytest.raises(tf.TFError) as ex:
             g.set_two_step(bad)
         assert ex.value.status == tf.TF_EINVAL
+
+
+@pytest.mark.parametrize("name", ["cpw-small", "cpml-xz-periodic-y", "periodic-xy-mur-z"])
+def test_item_length_gives_the_same_bits(name):
+    """The single-step kernel's work-item length (tf_set_item_planes: 8 .. 16
+    planes per item, in single steps and in the shell of two-step passes)
+    changes how the work is cut, not the bits; out-of-range lengths are
+    refused."""
+    from paper_2305_13419_gb300 import twofluid as tf
+    w = CASES[name]()
+    st = None if name.startswith("cpw") else W.random_state(7, w.storage_dims())
+    for two in (False, True):
+        ref = _run(w, two, [23], st)
+        for planes in (12, 16):
+            g = tf.Grid.from_workload(w)
+            g.set_two_step(two)
+            g.set_item_planes(planes)
+            if st is not None:
+                for c in range(9):
+                    g.set_field(c, st[c].astype(np.float32))
+            g.step(23)
+            g.sync()
+            for c in range(9):
+                assert np.array_equal(g.field(c), ref.field(c)), (name, two, planes, c)
+            for p in range(len(w.probes)):
+                assert np.array_equal(g.probe_dft(p), ref.probe_dft(p))
+    for bad in (7, 17):
+        with pytest.raises(tf.TFError) as ex:
+            g.set_item_planes(bad)
+        assert ex.value.status == tf.TF_EINVAL
