@@ -331,7 +331,7 @@ def config_block(state_bytes=None):
     return c
 
 
-def roofline_of(w, g, kt, planes=16, item_planes=8):
+def roofline_of(w, g, kt, planes=24, item_planes=8):
     """Roofline of the step kernels from their algorithmic bytes per launch
     over their mean event-timed launch durations, against the measured HBM
     peak.  With two-step passes the two-step kernel (the interior box, two
@@ -418,7 +418,7 @@ def run_ours(args, ws, rank, local):
     g.sync()
     ms_max = max_over_ranks(dist, ms, dev)
     value = aggregate(w.ncells, args.steps, ms_max, ws)
-    ab, roof = roofline_of(w, g, kt, planes=tuning["best"] if tuning and tuning["best"] else 16,
+    ab, roof = roofline_of(w, g, kt, planes=tuning["best"] if tuning and tuning["best"] else 24,
                            item_planes=tuning["item_planes"] if tuning else (args.item_planes or 8))
     state_bytes = (9 + 3) * 4 * ab["points"]
     launches = sum(v[1] for v in kt.values())
@@ -654,7 +654,7 @@ def run_config(w, steps, warmup=5, two_step=True, autotune_steps=0):
     torch.cuda.synchronize()
     kt, ms = g.step_timed(steps, with_total=True)
     g.sync()
-    _, roof = roofline_of(w, g, kt, planes=tuning["best"] if tuning and tuning["best"] else 16,
+    _, roof = roofline_of(w, g, kt, planes=tuning["best"] if tuning and tuning["best"] else 24,
                           item_planes=tuning["item_planes"] if tuning else 8)
     g.close()
     del g

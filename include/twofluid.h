@@ -189,8 +189,8 @@ tf_status tf_step_timed(tf_handle h, int64_t nsteps, double* kernel_ms, int64_t*
  * same bits as single steps.  It is used when the box is not empty, mu is
  * uniform (tf_set_materials) and it is enabled; an odd step count ends with a
  * single step.
- *   tf_set_two_step  planes = 0 disables it for this handle; 4 .. 16 enables
- *                    it with work items of that many planes (16 by default);
+ *   tf_set_two_step  planes = 0 disables it for this handle; 4 .. 24 enables
+ *                    it with work items of that many planes (24 by default);
  *                    other values TF_EINVAL.  A tuning switch (the project's
  *                    autotuner sets it per grid): results do not change.
  *   tf_two_step_box  the box in storage points, [lo, hi) per axis (all zero

@@ -5,8 +5,8 @@ Every setting gives the same bits (the step's arithmetic does not depend on
 how the work is cut), so the tuner only times.  What it chooses:
 
   * temporal-block depth per grid: single steps (T = 1) or two steps per
-    pass over the interior box (T = 2) with two-step work items of 8, 12 or
-    16 planes (tf_set_two_step);
+    pass over the interior box (T = 2) with two-step work items of 8 to 24
+    planes (tf_set_two_step);
   * the single-step kernel's work-item length, 8 or 16 planes
     (tf_set_item_planes): long items on large grids, short ones where a
     grid has few items per CTA.
@@ -23,7 +23,7 @@ from __future__ import annotations
 import json
 from typing import Dict, Iterable
 
-TWO_STEP_CANDIDATES = (0, 8, 12, 16)   # 0: single steps; else planes per two-step work item
+TWO_STEP_CANDIDATES = (0, 8, 12, 16, 20, 24)   # 0: single steps; else planes per two-step work item
 ITEM_PLANES_CANDIDATES = (8, 16)       # planes per single-step work item
 
 

@@ -421,7 +421,7 @@ tf_status tf_create(const tf_grid_desc* desc, void* dev_workspace, size_t bytes,
     h->ctr_t = (unsigned long long*)(base + L.off_misc + 160);
     h->base_t = 0;
     h->two_step_on = 1;
-    h->tb_len = kTBLenMax;
+    h->tb_len = kTBLenDefault;
     h->item_planes = kChunk;
     P.status = h->status;
     P.wait_polls = kSpinLimit;

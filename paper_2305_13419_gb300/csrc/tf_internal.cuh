@@ -163,7 +163,8 @@ struct Probes {
 // n+1 E / n+1/2 B of the points within two of the box faces (and of probe
 // points) to the third buffer, from which the single-step kernel advances
 // the rest of the grid to level n+2.
-constexpr int kTBLenMax = 16, kTBLenMin = 4;   // planes per two-step work item (the default is the maximum)
+constexpr int kTBLenMax = 24, kTBLenMin = 4;   // planes per two-step work item
+constexpr int kTBLenDefault = 24;
 struct Step2Out {
     float* E[3];             // E^{n+2}, B^{n+3/2}, Jt^{n+3/2}
     float* B[3];

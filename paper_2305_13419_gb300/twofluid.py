@@ -463,10 +463,10 @@ class Grid:
 
     def set_two_step(self, planes):
         """Two-step passes (temporal blocking): False / 0 forbids them, True
-        allows them with 16-plane work items (the default), 4 .. 16 sets the
+        allows them with 24-plane work items (the default), 4 .. 24 sets the
         work-item length."""
         if planes is True:
-            planes = 16
+            planes = 24
         _check(load().tf_set_two_step(self.h, int(planes or 0)), "tf_set_two_step")
 
     def set_item_planes(self, planes: int):

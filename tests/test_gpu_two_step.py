@@ -93,10 +93,10 @@ def test_non_uniform_mu_keeps_single_steps():
     assert "step2" not in kt and kt["step"][1] == 4
 
 
-@pytest.mark.parametrize("planes", [4, 7, 12])
+@pytest.mark.parametrize("planes", [4, 7, 12, 24])
 def test_two_step_item_lengths_give_the_same_bits(planes):
     """The autotuner's knob: every two-step work-item length gives the bits
-    of single steps; lengths outside 4 .. 16 are rejected."""
+    of single steps; lengths outside 4 .. 24 are rejected."""
     from paper_2305_13419_gb300 import twofluid as tf
     w = _cpw_with_inner_source()
     ref = _run(w, False, [21], None)
@@ -107,7 +107,7 @@ def test_two_step_item_lengths_give_the_same_bits(planes):
     assert g.two_step_box()[1]
     for c in range(9):
         assert np.array_equal(g.field(c), ref.field(c)), c
-    for bad in (1, 3, 17):
+    for bad in (1, 3, 25):
         with pytest.raises(tf.TFError) as ex:
             g.set_two_step(bad)
         assert ex.value.status == tf.TF_EINVAL
