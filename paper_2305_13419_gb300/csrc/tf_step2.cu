@@ -14,7 +14,7 @@
 //
 // Work layout.  A CTA of 256 threads owns a 32 x 16 column tile (as the
 // single-step kernel) and streams it along z through a work item of up to
-// 16 planes.  E^n and B^{n-1/2} of each plane land by TMA boxes (x0-4 ..
+// 24 planes.  E^n and B^{n-1/2} of each plane land by TMA boxes (x0-4 ..
 // x0+35, y0-2 .. y0+17 / y0+16) through a ring of four mbarrier-guarded
 // stages filled by one producer thread that runs ahead into the next item.
 // The first step is formed on the tile plus a two-point halo, the second on
